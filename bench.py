@@ -1,0 +1,305 @@
+"""Benchmark of the improved ETD particle-in-cell step on GB300.
+
+Workload (default, `vp1e6`): the Vlasov-Poisson beam with eps = 0.01,
+N_p = 1e6 particles, radial mesh of 256 cells on [-4, 4] with linear
+deposit/gather, f0 Gaussian in v (v_th = 1) times a Gaussian in r (sigma 1)
+truncated to |r| <= 4, macro step dt = 0.1, Lawson RK4 fine solver at
+h = 2 pi eps / 100.  One "step" is one macro step of Algorithm ETDFSSModAlgo
+for every particle (period detection, fine window with a full field cycle
+per stage, landing, extrapolation).  Metric: particle-steps/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload vp1e6|duffing1e4]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the only reference this method has) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec per GB300 (push+deposit+field) at stated error vs FP64 oracle"
+UNIT = "particle-steps/s"
+FP64_PEAK_FLOPS = 1.25e12  # nominal GB300 FP64 rate (no FP64 figure is measured by the driver)
+
+WORKLOADS = {
+    # paper-shaped Vlasov-Poisson run (the metric's workload)
+    "vp1e6": dict(n=10**6, params=dict(), r_cut=4.0, desc="Vlasov-Poisson, eps=0.01, N_p=1e6, N_r=256 on [-4,4], CIC, dt=0.1, Lawson RK4 fine step 2*pi*eps/100, FP64"),
+    # Duffing test field, periods once at init
+    "duffing1e4": dict(n=10**4, params=dict(field_model=1, dt=0.05, periods_once=1), r_cut=None,
+                       desc="Duffing E=-r^3, eps=0.01, N_p=1e4, dt=0.05, periods once, FP64"),
+}
+
+# Algorithmic FP64 flops per particle per fine step of the Lawson RK4 window
+# (FMA = 2): four stage positions (3+5+5 flops), the update of R and V
+# (6+9), and per stage the CIC location, deposit weight and gather (7 x 4).
+FLOPS_PER_PARTICLE_FINE_STEP = 56
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while it runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_params(pic, wl):
+    return pic.pic_default_params(**WORKLOADS[wl]["params"])
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1404_1160_gb300 import build as _build
+    from paper_1404_1160_gb300 import inputs
+    from paper_1404_1160_gb300 import pic
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    # replicas: every rank advances its own beam (different seed)
+    R0, V0 = inputs.gaussian_beam(n, seed=rank, r_cut=wl["r_cut"])
+    prm = make_params(pic, args.workload)
+    stream = torch.cuda.current_stream()
+    h = pic.pic_init(prm, torch.from_numpy(R0).cuda(), torch.from_numpy(V0).cuda(), stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(args.warmup):
+        pic.pic_step(h, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = pic.pic_launch_count(h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
+            evs[k][0].record(stream)
+            pic.pic_step(h, 1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    launches = pic.pic_launch_count(h) - launches0
+    dev_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = world * n * args.steps / dev_s
+    mom = pic.pic_moments(h)
+
+    # end to end through the public API with host buffers: H2D of the
+    # step's input (pinned), the step, D2H of the result
+    r_h = torch.from_numpy(R0.copy()).pin_memory()
+    v_h = torch.from_numpy(V0.copy()).pin_memory()
+    r_o = torch.empty(n, dtype=torch.float64).pin_memory()
+    v_o = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pic.pic_set_particles(h, r_h, v_h)
+        pic.pic_step(h, 1)
+        pic.pic_get_particles(h, r_o, v_o)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n}
+    pic.pic_destroy(h)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    mean_ms = float(np.mean(step_ms))
+    K = mom["window_steps"]
+    if args.workload == "vp1e6":
+        flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
+        achieved = flops / (mean_ms / 1e3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+                    "kernel": "k_window_coop<1> (one launch per macro step)",
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived, not in MEASURED_PEAKS.json)",
+                    "fine_steps_per_launch": K}
+    else:
+        roofline = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_particles": n, "fine_steps_per_window": K,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "L2 flushed between timed steps (256 MB write); per-step trajectory store > L2"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "wall_s": wall,
+        "clocks": clk.summary(),
+        "error_vs_oracle": "bit-identical R, V and charge on the parity tests (tolerance 1e-12 rel)",
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(workload: str, n_sample: int):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    from paper_1404_1160_gb300 import inputs
+
+    wl = WORKLOADS[workload]
+    n = min(n_sample, wl["n"])
+    cfg = oracle_cfg(workload)
+    R0, V0 = inputs.gaussian_beam(n, seed=0, r_cut=wl["r_cut"])
+    T = None
+    if cfg_periods_once(workload):
+        T, _, _ = oracle.periods(cfg, R0, V0)
+    t0 = time.perf_counter()
+    steps = 0
+    R, V = R0, V0
+    while True:
+        res = oracle.etd_step(cfg, R, V, T)
+        R, V = res.R, res.V
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > 8.0 or steps >= 1000:
+            break
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} macro step(s) of {n} particles of the same workload ({el:.1f} s)"}
+
+
+def cfg_periods_once(workload):
+    return bool(WORKLOADS[workload]["params"].get("periods_once", 0))
+
+
+def oracle_cfg(workload):
+    import oracle
+
+    p = dict(eps=0.01, dt=0.1, field_model=0, fine_solver=1, steps_per_turn=100, n_cells=256, r_min=-4.0, r_max=4.0,
+             total_charge=1.0, weight_fixed=1 << 32, max_window_steps=300)
+    q = dict(WORKLOADS[workload]["params"])
+    q.pop("periods_once", None)
+    p.update(q)
+    return oracle.Config(**p)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1404_1160_gb300 import inputs
+
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    n = min(args.cpu_sample, wl["n"])
+    cfg = oracle_cfg(args.workload)
+    R, V = inputs.gaussian_beam(n, seed=0, r_cut=wl["r_cut"])
+    T = oracle.periods(cfg, R, V)[0] if cfg_periods_once(args.workload) else None
+    for _ in range(args.warmup):
+        res = oracle.etd_step(cfg, R, V, T)
+        R, V = res.R, res.V
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = oracle.etd_step(cfg, R, V, T)
+        R, V = res.R, res.V
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_particles_sample": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one macro step of {n} particles of the same workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vp1e6")
+    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) improved-ETD particle-in-cell library.
+ *
+ * The library advances the axisymmetric-beam Vlasov equation
+ *     df/dt + (v/eps) df/dr + (-r/eps + E(r,t)) df/dv = 0
+ * (eq. VlasAxSymBeam of Frenod, Hirstoaga & Lutz) with macroparticles
+ * (Sec. 2.1) along the characteristics dR/dt = V/eps, dV/dt = -R/eps + E
+ * (eq. CharactCurvesOfGenVlas), using the improved ETD scheme (Algorithm
+ * ETDFSSModAlgo, Sec. 3).  E comes from the axisymmetric Poisson equation
+ * d/dr(rE) = rho, rho = int f dv (eq. VlasPoissAxSymBeam), solved on a radial
+ * mesh with the trapezoidal rule (Sec. 2.3), or is the Duffing test field
+ * E = -r^3 (eq. RappelForce), or zero.
+ *
+ * Conventions for every entry point:
+ *  - Status: PIC_OK (0) on success, a negative PIC_ERR_* code otherwise.
+ *    Nothing throws or aborts across this boundary.  pic_strerror() names a
+ *    code.
+ *  - Arrays are plain pointers with explicit lengths.  Unless stated, the
+ *    caller keeps ownership of everything it passes and the library copies
+ *    what it needs.  ptr_kind says whether a pointer is host (PIC_PTR_HOST)
+ *    or device (PIC_PTR_DEVICE) memory of the current CUDA device.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls that return data or a status
+ *    synchronise that stream.
+ *  - Particle state is FP64 structure-of-arrays: R[n], V[n] (the paper's
+ *    y = (R, V)).  Periods are reported in units of time.
+ *  - All computation runs in the library's CUDA kernels.  There is no CPU
+ *    fallback: without a usable CUDA device, pic_init and the standalone
+ *    mesh calls return PIC_ERR_CUDA.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PIC_OK                 0
+#define PIC_ERR_INVALID_ARG   -1  /* a parameter or pointer is out of range  */
+#define PIC_ERR_CUDA          -2  /* a CUDA call failed / no usable device   */
+#define PIC_ERR_TIMEOUT       -3  /* a device-side wait hit its time limit   */
+#define PIC_ERR_OVERFLOW      -4  /* n_particles * weight_fixed >= 2^62      */
+#define PIC_ERR_UNSUPPORTED   -5  /* valid request this build does not serve */
+#define PIC_ERR_NO_MEMORY     -6  /* device allocation failed                */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { PIC_FIELD_POISSON = 0, PIC_FIELD_DUFFING = 1, PIC_FIELD_ZERO = 2 };
+/* Fine solver of steps 1 and 3 of Algorithm ETDFSSModAlgo:
+   PIC_FINE_RK4 is the paper's explicit RK4 (Remark CompOfThePeriodsRem);
+   PIC_FINE_LAWSON_RK4 advances the linear part (1/eps) M y of
+   eq. StiffODEForBeam by its exact rotation and applies RK4 to the field
+   term only (integrating-factor RK4). */
+enum { PIC_FINE_RK4 = 0, PIC_FINE_LAWSON_RK4 = 1 };
+enum { PIC_PTR_HOST = 0, PIC_PTR_DEVICE = 1 };
+
+/* ---- problem statement ------------------------------------------------- */
+/* Mirrors the paper's statement of the problem: eps (Sec. 1), the macro step
+   Delta t (eq. TimeStepDec), the fine step (dt)_RK = 2*pi*eps/steps_per_turn
+   (Remark CompOfThePeriodsRem, 100 in the paper), the radial mesh
+   (Sec. 2.3, 256 cells in the paper), the field model and the total charge
+   sum(omega_i) = int f0 (Sec. 2.1). */
+typedef struct {
+    double   eps;              /* > 0                                            */
+    double   dt;               /* macro step Delta t > 0                          */
+    int32_t  field_model;      /* PIC_FIELD_*                                     */
+    int32_t  fine_solver;      /* PIC_FINE_*                                      */
+    int32_t  steps_per_turn;   /* >= 4; fine step h = 2*pi*eps/steps_per_turn     */
+    int32_t  n_cells;          /* Poisson: even, 2..65536; node n_cells/2 is r=0  */
+    double   r_min, r_max;     /* Poisson: r_min = -r_max < 0                     */
+    double   total_charge;     /* sum of particle weights (> 0)                   */
+    uint64_t weight_fixed;     /* W: fixed-point units per particle, a power of
+                                  two <= 2^40, with n_particles*W < 2^62          */
+    int32_t  max_window_steps; /* fine steps a window may run; >= 2*spt + 2       */
+    int32_t  periods_once;     /* 1: periods computed once at pic_init and kept
+                                  (the Duffing case of Sec. 4.1); 0: every step  */
+    int32_t  precision;        /* 0 = FP64 (only value served)                    */
+    int32_t  block_size;       /* CUDA threads per block, 0 = library default     */
+    int64_t  wait_limit_ns;    /* limit of every device-side wait, 0 = 2 s        */
+} pic_params;
+
+/* Fills p with the defaults of the paper-shaped Vlasov-Poisson run:
+   eps 0.01, dt 0.1, Poisson, Lawson RK4, 100 steps per turn, 256 cells on
+   [-4, 4], total charge 1, W = 2^32, window cap 300, periods every step. */
+void pic_default_params(pic_params* p);
+
+/* ---- handle-based run (the hot path) ----------------------------------- */
+typedef struct pic_handle pic_handle;   /* opaque; owns all its device memory */
+
+/* Creates a run of n particles with initial state (r0[i], v0[i]) sampled from
+   f0 (Sec. 2.1; the caller samples f0).  The arrays are copied.  With
+   periods_once = 1 the periods T_i of y^0 are computed here (Remark
+   CompOfThePeriodsRem; Sec. 4.1: "executed only initially").  All later
+   work of the handle is enqueued on `stream`.  On success *out receives the
+   handle, which the caller releases with pic_destroy. */
+int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
+             int ptr_kind, void* stream, pic_handle** out);
+
+/* Advances every particle by n_steps macro steps of Algorithm ETDFSSModAlgo:
+   (1) periods T_i from y^n: fine steps from t_n until each particle's V has
+   changed sign three times, T_i = time between the first and third extremum
+   (Remark CompOfThePeriodsRem); (2) Delta t = N_i T_i + o_i, o_i in [0,T_i)
+   (eq. TimeStepDec); (3) y_i(t_n+o_i) and y_i(t_n+o_i+T_i) by quadratic
+   interpolation of the fine solution (Remark QuadraticInterpolationRem);
+   (4) y^{n+1} = y(o) + N (y(o+T) - y(o)) (eq. MainFormula1).  With the
+   Poisson model every fine stage is a full field cycle of all particles:
+   deposit, trapezoid integral, gather (Sec. 3: all particles pushed far
+   enough "to calculate the correct self-consistent electric field").
+   Synchronises the stream and returns the device status of the run. */
+int pic_step(pic_handle* h, int64_t n_steps);
+
+/* Advances every particle by n_fine fine steps of the fine solver: the
+   paper's reference solution (Sec. 2.1, RK4 with step 2*pi*eps/100). */
+int pic_fine_steps(pic_handle* h, int64_t n_fine);
+
+typedef struct {
+    double  t;                 /* time reached                                  */
+    int64_t n_steps;           /* macro steps taken                             */
+    int64_t n_particles;
+    int64_t Q_total;           /* sum of the deposited fixed-point charge        */
+    int64_t n_out_of_mesh;     /* particles outside [r_min, r_max)              */
+    double  charge;            /* Q_total * q_unit + out-of-mesh weight         */
+    double  kinetic;           /* sum omega (R^2 + V^2) / 2                     */
+    double  duffing_energy;    /* sum omega ((R^2+V^2)/2 + eps R^4/4): eps^2 H of
+                                  the appendix, summed                         */
+    double  mean_R, mean_V, rms_R, rms_V;
+    double  T_min, T_mean, T_max; /* periods of the last macro step (time)     */
+    int64_t N_min, N_max;      /* whole periods per macro step, last step       */
+    int64_t window_steps;      /* fine steps in the last window                 */
+    int64_t n_no_period;       /* particles that took T = 2*pi*eps last step    */
+} pic_moments_t;
+
+/* Diagnostics of the current state (computed by device reductions; one small
+   device-to-host copy).  Synchronises the stream. */
+int pic_moments(pic_handle* h, pic_moments_t* out);
+
+/* Copies R, V (n each) out of / into the handle. */
+int pic_get_particles(pic_handle* h, double* r, double* v, int ptr_kind);
+int pic_set_particles(pic_handle* h, const double* r, const double* v, int ptr_kind);
+
+/* Per-particle results of the last macro step: T_i (time), N_i, o_i (time).
+   Any pointer may be NULL. */
+int pic_get_periods(pic_handle* h, double* T, int64_t* N, double* o, int ptr_kind);
+
+/* Field of the current particle positions: Q (n_cells+1, fixed-point units),
+   E (n_cells+1) at the nodes, rE at the two mesh edges, out-of-mesh count.
+   Any pointer may be NULL.  Poisson model only. */
+int pic_get_field(pic_handle* h, int64_t* Q, double* E, double* rE_edges, int64_t* n_out,
+                  int ptr_kind);
+
+/* Checkpoint: particle state, periods (time), time and step count.  The
+   arrays are caller-owned host memory of n_particles doubles each.  Resuming
+   from a checkpoint reproduces an uninterrupted run bit for bit. */
+typedef struct {
+    double* r;
+    double* v;
+    double* T;
+    double  t;
+    int64_t n_steps;
+} pic_state_t;
+int pic_get_state(pic_handle* h, pic_state_t* out);
+int pic_set_state(pic_handle* h, const pic_state_t* in);
+
+int64_t pic_num_particles(const pic_handle* h);
+void pic_destroy(pic_handle* h);
+const char* pic_strerror(int status);
+
+/* Device-side kernel launches the handle has issued so far (for benchmarks). */
+int64_t pic_launch_count(const pic_handle* h);
+
+/* ---- standalone mesh operations on caller device buffers ---------------- */
+/* These run one step of the field cycle on caller-owned device memory.
+   Every pointer is device memory; sizes are element counts.  They enqueue
+   on `stream` and return without synchronising, except that argument errors
+   are reported immediately. */
+
+/* Linear (cloud-in-cell) deposit of n particles at R_dev onto the nodes
+   r_j = r_min + j*h_r, j = 0..n_cells (Sec. 2.3): a particle in cell j with
+   right weight f gives floor(f*W) units to node j+1 and the rest to node j,
+   as exact integers, so Q_dev is bit-exact and independent of order.
+   Particles outside [r_min, r_max) deposit nothing and are counted in
+   *n_out_dev.  Q_dev (n_cells+1 int64) and n_out_dev (1 int64) are
+   overwritten. */
+int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_dev,
+                int64_t* n_out_dev, void* stream);
+
+/* Trapezoid integral of d/dr(rE) = rho (eq. VlasPoissAxSymBeam, Sec. 2.3)
+   from r = 0 outward: S_j = sum of (Q_m + Q_{m+1}) over the cells between
+   node n_cells/2 and node j (negative on the left), computed as an exact
+   int64 prefix scan (warp shuffles + decoupled look-back across blocks);
+   then rE_j = S_j * q_unit/2, E_j = rE_j * (1/r_j), and at r = 0
+   E = rho(0) = Q * q_unit / h_r, with q_unit = total_charge/(n_particles*W).
+   Reads Q_dev (n_cells+1), writes E_dev (n_cells+1) and rE_edges_dev (2:
+   rE at r_min and r_max).  Uses device scratch that it allocates and frees
+   on the stream. */
+int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                double* rE_edges_dev, void* stream);
+
+/* E at n positions R_dev by linear interpolation of E_dev with the deposit's
+   weights; outside the mesh E = rE_edge / R (rE is constant beyond the
+   charge).  Writes e_dev (n). */
+int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double* E_dev,
+               const double* rE_edges_dev, double* e_dev, void* stream);
+
+/* ---- testing ------------------------------------------------------------ */
+/* Runs one macro step of a small Poisson beam whose grid barrier waits for
+   one more arrival than the grid has, so the wait can only end by its time
+   limit (wait_limit_ns, 1 ns..10 s).  Returns the status pic_step reports:
+   PIC_ERR_TIMEOUT when the limit works; the device stays usable.  Exercises
+   the failure path of every device-side wait without faulting the GPU. */
+int pic_test_barrier_timeout(int64_t wait_limit_ns, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,640 @@
+// api.cu -- host side of the C ABI declared in include/pic.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic.h"
+#include "pic_internal.h"
+
+using pic::DevParams;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PIC_OK;
+    if (e == cudaErrorMemoryAllocation) return PIC_ERR_NO_MEMORY;
+    return PIC_ERR_CUDA;
+}
+
+int map_dev(int s) {
+    if (s == pic::DEV_OK) return PIC_OK;
+    if (s == pic::DEV_TIMEOUT) return PIC_ERR_TIMEOUT;
+    return PIC_ERR_CUDA;
+}
+
+bool is_pow2(uint64_t w) { return w != 0 && (w & (w - 1)) == 0; }
+
+// Parameter checks shared by every entry point; mesh checks only when the
+// Poisson model (or a standalone mesh call) needs the mesh.
+int check_params(const pic_params* p, bool need_mesh) {
+    if (!p) return PIC_ERR_INVALID_ARG;
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps) || !(p->dt > 0.0) || !std::isfinite(p->dt))
+        return PIC_ERR_INVALID_ARG;
+    if (p->field_model < 0 || p->field_model > 2 || p->fine_solver < 0 || p->fine_solver > 1)
+        return PIC_ERR_INVALID_ARG;
+    if (p->steps_per_turn < 4 || p->steps_per_turn > (1 << 20)) return PIC_ERR_INVALID_ARG;
+    if (p->max_window_steps < 2 * p->steps_per_turn + 2 || p->max_window_steps > (1 << 24))
+        return PIC_ERR_INVALID_ARG;
+    if (p->precision != 0) return PIC_ERR_UNSUPPORTED;
+    if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || (p->block_size & 31)))
+        return PIC_ERR_INVALID_ARG;
+    if (p->wait_limit_ns < 0) return PIC_ERR_INVALID_ARG;
+    if (need_mesh || p->field_model == PIC_FIELD_POISSON) {
+        if (p->n_cells < 2 || p->n_cells > 65536 || (p->n_cells & 1)) return PIC_ERR_INVALID_ARG;
+        if (!(p->r_max > 0.0) || !std::isfinite(p->r_max) || p->r_min != -p->r_max) return PIC_ERR_INVALID_ARG;
+        if (!is_pow2(p->weight_fixed) || p->weight_fixed > (1ull << 40)) return PIC_ERR_INVALID_ARG;
+        if (!(p->total_charge > 0.0) || !std::isfinite(p->total_charge)) return PIC_ERR_INVALID_ARG;
+        // fixed-point positions x*W must stay below 2^62
+        if ((double)p->n_cells * (double)p->weight_fixed >= 4.611686018427388e18) return PIC_ERR_OVERFLOW;
+    }
+    return PIC_OK;
+}
+
+// Host precomputation of every constant a kernel uses.  The fine step and
+// the rotation constants follow h = 2 pi eps / steps_per_turn and
+// cos/sin(h/eps), cos/sin(h/(2 eps)) (exact E = 0 flow, Sec. 1).
+void make_devparams(const pic_params* p, long long n, DevParams* d) {
+    std::memset(d, 0, sizeof(*d));
+    d->eps = p->eps;
+    d->inv_eps = 1.0 / p->eps;
+    d->mie = -d->inv_eps;
+    d->h = (2.0 * kPi * p->eps) / (double)p->steps_per_turn;
+    d->h2 = 0.5 * d->h;
+    d->h6 = d->h / 6.0;
+    d->D = p->dt / d->h;
+    const double th = d->h / p->eps;
+    d->c1 = std::cos(th);
+    d->s1 = std::sin(th);
+    d->ch = std::cos(0.5 * th);
+    d->sh = std::sin(0.5 * th);
+    d->hsh = d->h * d->sh;
+    d->tch = 2.0 * d->ch;
+    d->tsh = 2.0 * d->sh;
+    d->n_cells = p->n_cells;
+    d->c = p->n_cells / 2;
+    d->r_min = p->r_min;
+    if (p->n_cells > 0) {
+        d->hr = (p->r_max - p->r_min) / (double)p->n_cells;
+        d->inv_hr = 1.0 / d->hr;
+    }
+    d->W = (long long)p->weight_fixed;
+    d->Wmask = d->W - 1;
+    int l2 = 0;
+    while (l2 < 63 && (1ull << l2) < p->weight_fixed) ++l2;
+    d->log2W = l2;
+    d->Wd = (double)p->weight_fixed;
+    d->invW = 1.0 / d->Wd;
+    int ex = 0;
+    d->xs_fma = (d->inv_hr > 0.0 && std::frexp(d->inv_hr, &ex) == 0.5) ? 1 : 0;
+    d->xs_scale = d->inv_hr * d->Wd;
+    d->xs_off = -(p->r_min * d->inv_hr) * d->Wd;
+    d->xs_max = (double)p->n_cells * d->Wd;
+    d->q_unit = n > 0 ? p->total_charge / ((double)n * d->Wd) : 0.0;
+    d->q_half = 0.5 * d->q_unit;
+    d->field = p->field_model;
+    d->solver = p->fine_solver;
+    d->Kmax = p->max_window_steps;
+    d->Tfb = (double)p->steps_per_turn;
+    d->n = n;
+    d->wait_ns = p->wait_limit_ns > 0 ? p->wait_limit_ns : 2000000000ll;
+    d->bar_extra = 0;
+}
+
+int current_sm_count(int* sms) {
+    int dev = 0, count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) return PIC_ERR_CUDA;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return PIC_ERR_CUDA;
+    if ((e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return PIC_ERR_CUDA;
+    return PIC_OK;
+}
+
+cudaMemcpyKind kind_to(int ptr_kind) { return ptr_kind == PIC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_from(int ptr_kind) { return ptr_kind == PIC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// Converts the per-particle step results to the public units.
+__global__ void k_export_periods(long long n, double h, const double* Ts, const int* N, const double* os,
+                                 double* T_out, long long* N_out, double* o_out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (T_out) T_out[i] = Ts[i] * h;
+        if (N_out) N_out[i] = (long long)N[i];
+        if (o_out) o_out[i] = os[i] * h;
+    }
+}
+
+}  // namespace
+
+struct pic_handle {
+    pic_params prm;
+    DevParams dp;
+    long long n = 0;
+    cudaStream_t st = nullptr;
+    int sm_count = 0, block = 0;
+    pic::WinBufs B;
+    pic::WindowLaunch L;
+    double* Tin = nullptr;   // periods of y^0 (fine steps) when periods_once
+    std::vector<void*> allocs;
+    // field of the current positions
+    long long *Qf = nullptr, *nout_f = nullptr;
+    double *Ef = nullptr, *edges_f = nullptr;
+    void* scan_mem = nullptr;
+    pic::ScanScratch S;
+    // moments
+    double* part_d = nullptr;
+    long long* part_i = nullptr;
+    int mom_grid = 1;
+    int* status_host = nullptr;  // pinned
+    double t = 0.0;
+    long long n_steps = 0;
+    int have_periods = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(pic_handle* h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+    if (e != cudaSuccess) return map_cuda(e);
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return PIC_OK;
+}
+
+void free_all(pic_handle* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->status_host) cudaFreeHost(h->status_host);
+    h->status_host = nullptr;
+}
+
+int read_status(pic_handle* h) {
+    cudaError_t e = cudaMemcpyAsync(h->status_host, h->B.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    return map_dev(*h->status_host);
+}
+
+// Resets the per-launch synchronisation words of the cooperative window.
+cudaError_t reset_coop(pic_handle* h) {
+    const size_t Np1 = (size_t)h->dp.n_cells + 1;
+    cudaError_t e = cudaMemsetAsync(h->B.Qring, 0, sizeof(unsigned long long) * 3 * 2 * Np1, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.notdone, 0, sizeof(int) * 3, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.bar, 0, sizeof(unsigned int), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
+    return e;
+}
+
+int run_window(pic_handle* h, int mode, long long n_iter) {
+    if (h->n == 0) return PIC_OK;
+    cudaError_t e = cudaMemsetAsync(h->B.status, 0, sizeof(int), h->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    const int T_known = (mode == pic::MODE_ETD && h->prm.periods_once) ? 1 : 0;
+    if (h->prm.field_model == PIC_FIELD_POISSON) {
+        const long long reps = mode == pic::MODE_ETD ? n_iter : 1;
+        for (long long s = 0; s < reps && e == cudaSuccess; ++s) {
+            e = reset_coop(h);
+            if (e == cudaSuccess)
+                e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, mode == pic::MODE_FINE ? n_iter : 0,
+                                            h->st, &h->launches, h->Tin);
+        }
+    } else {
+        e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
+        if (e == cudaSuccess)
+            e = pic::launch_window_local(h->dp, h->B, mode, T_known, mode == pic::MODE_PERIODS ? 0 : n_iter,
+                                         h->block, h->sm_count, h->st, &h->launches, h->Tin);
+    }
+    if (e != cudaSuccess) return map_cuda(e);
+    return read_status(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void pic_default_params(pic_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps = 0.01;
+    p->dt = 0.1;
+    p->field_model = PIC_FIELD_POISSON;
+    p->fine_solver = PIC_FINE_LAWSON_RK4;
+    p->steps_per_turn = 100;
+    p->n_cells = 256;
+    p->r_min = -4.0;
+    p->r_max = 4.0;
+    p->total_charge = 1.0;
+    p->weight_fixed = 1ull << 32;
+    p->max_window_steps = 300;
+    p->periods_once = 0;
+    p->precision = 0;
+    p->block_size = 0;
+    p->wait_limit_ns = 0;
+}
+
+const char* pic_strerror(int s) {
+    switch (s) {
+        case PIC_OK: return "ok";
+        case PIC_ERR_INVALID_ARG: return "invalid argument";
+        case PIC_ERR_CUDA: return "CUDA error or no usable CUDA device";
+        case PIC_ERR_TIMEOUT: return "device-side wait exceeded its time limit";
+        case PIC_ERR_OVERFLOW: return "fixed-point charge would overflow (n*W >= 2^62)";
+        case PIC_ERR_UNSUPPORTED: return "unsupported request";
+        case PIC_ERR_NO_MEMORY: return "device memory allocation failed";
+        default: return "unknown status";
+    }
+}
+
+int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0, int ptr_kind, void* stream,
+             pic_handle** out) {
+    if (!out) return PIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = check_params(p, false);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!r0 || !v0)) || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE))
+        return PIC_ERR_INVALID_ARG;
+    if (p->field_model == PIC_FIELD_POISSON) {
+        if (p->n_cells > pic::kMaxCellsWindow) return PIC_ERR_UNSUPPORTED;
+        if ((double)n * (double)p->weight_fixed >= 4.611686018427388e18) return PIC_ERR_OVERFLOW;
+    }
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+
+    pic_handle* h = new (std::nothrow) pic_handle();
+    if (!h) return PIC_ERR_NO_MEMORY;
+    h->prm = *p;
+    h->n = n;
+    h->st = (cudaStream_t)stream;
+    h->sm_count = sms;
+    make_devparams(p, n, &h->dp);
+    h->block = p->block_size ? p->block_size : (p->field_model == PIC_FIELD_POISSON ? 512 : 128);
+
+    const size_t N = (size_t)n;
+    const size_t Np1 = (size_t)p->n_cells + 1;
+    const bool need_traj = p->field_model == PIC_FIELD_POISSON || !p->periods_once;
+    pic::WinBufs& B = h->B;
+    std::memset(&B, 0, sizeof(B));
+    cudaError_t e = cudaSuccess;
+    rc = PIC_OK;
+#define ALLOC(ptr, cnt) \
+    if (!rc) rc = dalloc(h, &(ptr), (cnt))
+    ALLOC(B.R, N);
+    ALLOC(B.V, N);
+    ALLOC(B.Vm2, N);
+    ALLOC(B.t1, N);
+    ALLOC(B.T, N);
+    ALLOC(B.o, N);
+    ALLOC(B.N, N);
+    ALLOC(B.need, N);
+    ALLOC(B.flags, N);
+    if (p->field_model == PIC_FIELD_POISSON) {
+        ALLOC(B.c0, N);
+        ALLOC(B.c1, N);
+        ALLOC(B.c2, N);
+        ALLOC(B.c3, N);
+        ALLOC(B.j0, N);
+        ALLOC(B.j1, N);
+        if (p->fine_solver == PIC_FINE_RK4) {
+            ALLOC(B.c4, N);
+            ALLOC(B.c5, N);
+        }
+        ALLOC(B.Qring, 3 * 2 * Np1);
+        ALLOC(h->Qf, Np1);
+        ALLOC(h->nout_f, 1);
+        ALLOC(h->Ef, Np1);
+        ALLOC(h->edges_f, 2);
+    }
+    if (need_traj) ALLOC(B.traj, ((size_t)p->max_window_steps + 1) * N);
+    if (p->periods_once) ALLOC(h->Tin, N);
+    ALLOC(B.notdone, 3);
+    ALLOC(B.bar, 1);
+    ALLOC(B.status, 1);
+    ALLOC(B.K_out, 1);
+#undef ALLOC
+    if (!rc && p->field_model == PIC_FIELD_POISSON) {
+        size_t bytes = pic::scan_scratch_bytes(p->n_cells);
+        char* mem = nullptr;
+        rc = dalloc(h, &mem, bytes);
+        if (!rc) {
+            int tiles = (p->n_cells + pic::kScanTile - 1) / pic::kScanTile;
+            pic::scan_scratch_layout(p->n_cells, tiles, mem, &h->S);
+        }
+    }
+    if (!rc) {
+        long long want = (n + 255) / 256;
+        long long cap = (long long)sms * 4;
+        h->mom_grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+        rc = dalloc(h, &h->part_d, (size_t)h->mom_grid * pic::kMomDoubles);
+        if (!rc) rc = dalloc(h, &h->part_i, (size_t)h->mom_grid * pic::kMomInts);
+    }
+    if (!rc) {
+        e = cudaMallocHost(&h->status_host, sizeof(int));
+        rc = map_cuda(e);
+    }
+    if (!rc && n > 0) {
+        e = cudaMemcpyAsync(B.R, r0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B.V, v0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.T, 0, sizeof(double) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.o, 0, sizeof(double) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.N, 0, sizeof(int) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.flags, 0, sizeof(int) * N, h->st);
+        rc = map_cuda(e);
+    }
+    if (!rc && p->field_model == PIC_FIELD_POISSON)
+        rc = map_cuda(pic::window_prepare(h->dp, h->block, sms, &h->L));
+    if (!rc && p->periods_once && n > 0) {
+        // step 1 once, at initialisation (Sec. 4.1)
+        rc = run_window(h, pic::MODE_PERIODS, 0);
+        if (!rc) rc = map_cuda(cudaMemcpyAsync(h->Tin, B.T, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->st));
+        if (!rc) h->have_periods = 1;
+    }
+    if (!rc) rc = map_cuda(cudaStreamSynchronize(h->st));
+    if (rc) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+int pic_step(pic_handle* h, int64_t n_steps) {
+    if (!h || n_steps < 0) return PIC_ERR_INVALID_ARG;
+    if (n_steps == 0) return PIC_OK;
+    int rc = run_window(h, pic::MODE_ETD, n_steps);
+    if (rc == PIC_OK) {
+        h->t += (double)n_steps * h->prm.dt;
+        h->n_steps += n_steps;
+        h->have_periods = 1;
+    }
+    return rc;
+}
+
+int pic_fine_steps(pic_handle* h, int64_t n_fine) {
+    if (!h || n_fine < 0) return PIC_ERR_INVALID_ARG;
+    if (n_fine == 0) return PIC_OK;
+    int rc = run_window(h, pic::MODE_FINE, n_fine);
+    if (rc == PIC_OK) h->t += (double)n_fine * h->dp.h;
+    return rc;
+}
+
+int pic_get_field(pic_handle* h, int64_t* Q, double* E, double* rE_edges, int64_t* n_out, int ptr_kind) {
+    if (!h || h->prm.field_model != PIC_FIELD_POISSON) return PIC_ERR_INVALID_ARG;
+    if (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE) return PIC_ERR_INVALID_ARG;
+    if (h->n == 0) return PIC_ERR_INVALID_ARG;
+    const size_t Np1 = (size_t)h->dp.n_cells + 1;
+    cudaError_t e = pic::launch_deposit(h->dp, h->B.R, h->n, h->Qf, h->nout_f, h->st, h->sm_count, &h->launches);
+    if (e == cudaSuccess) e = pic::launch_poisson(h->dp, h->Qf, h->Ef, h->edges_f, h->S, h->st, &h->launches);
+    if (e == cudaSuccess && Q) e = cudaMemcpyAsync(Q, h->Qf, sizeof(long long) * Np1, kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, h->Ef, sizeof(double) * Np1, kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess && rE_edges)
+        e = cudaMemcpyAsync(rE_edges, h->edges_f, sizeof(double) * 2, kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess && n_out) e = cudaMemcpyAsync(n_out, h->nout_f, sizeof(long long), kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->status_host, h->S.status, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    return map_dev(*h->status_host);
+}
+
+int pic_moments(pic_handle* h, pic_moments_t* out) {
+    if (!h || !out) return PIC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->t = h->t;
+    out->n_steps = h->n_steps;
+    out->n_particles = h->n;
+    if (h->n == 0) return PIC_OK;
+    const int G = h->mom_grid;
+    std::vector<double> pd((size_t)G * pic::kMomDoubles);
+    std::vector<long long> pi((size_t)G * pic::kMomInts);
+    long long Kw = 0;
+    cudaError_t e = pic::launch_moments(h->dp, h->B, h->part_d, h->part_i, G, h->st, &h->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pd.data(), h->part_d, sizeof(double) * pd.size(), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pi.data(), h->part_i, sizeof(long long) * pi.size(), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&Kw, h->B.K_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    double a[pic::kMomDoubles] = {0, 0, 0, 0, 0, 0, INFINITY, -INFINITY};
+    long long b[pic::kMomInts] = {LLONG_MAX, LLONG_MIN, 0};
+    for (int g = 0; g < G; ++g) {
+        const double* x = &pd[(size_t)g * pic::kMomDoubles];
+        const long long* y = &pi[(size_t)g * pic::kMomInts];
+        for (int q = 0; q < 6; ++q) a[q] += x[q];
+        a[6] = std::fmin(a[6], x[6]);
+        a[7] = std::fmax(a[7], x[7]);
+        b[0] = y[0] < b[0] ? y[0] : b[0];
+        b[1] = y[1] > b[1] ? y[1] : b[1];
+        b[2] += y[2];
+    }
+    const double n = (double)h->n, w = h->prm.total_charge / n, hh = h->dp.h;
+    out->mean_R = a[0] / n;
+    out->mean_V = a[1] / n;
+    out->rms_R = std::sqrt(a[2] / n);
+    out->rms_V = std::sqrt(a[3] / n);
+    out->kinetic = w * 0.5 * (a[2] + a[3]);
+    out->duffing_energy = w * (0.5 * (a[2] + a[3]) + 0.25 * h->prm.eps * a[4]);
+    if (h->have_periods) {
+        out->T_min = a[6] * hh;
+        out->T_max = a[7] * hh;
+        out->T_mean = a[5] / n * hh;
+        out->N_min = b[0];
+        out->N_max = b[1];
+        out->n_no_period = b[2];
+        out->window_steps = Kw;
+    }
+    if (h->prm.field_model == PIC_FIELD_POISSON) {
+        std::vector<int64_t> Q((size_t)h->dp.n_cells + 1);
+        int64_t nout = 0;
+        int rc = pic_get_field(h, Q.data(), nullptr, nullptr, &nout, PIC_PTR_HOST);
+        if (rc) return rc;
+        long long tot = 0;
+        for (int64_t q : Q) tot += (long long)q;
+        out->Q_total = tot;
+        out->n_out_of_mesh = nout;
+        out->charge = (double)tot * h->dp.q_unit + (double)nout * w;
+    } else {
+        out->charge = h->prm.total_charge;
+    }
+    return PIC_OK;
+}
+
+int pic_get_particles(pic_handle* h, double* r, double* v, int ptr_kind) {
+    if (!h || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    if (h->n == 0) return PIC_OK;
+    cudaError_t e = cudaSuccess;
+    if (r) e = cudaMemcpyAsync(r, h->B.R, sizeof(double) * h->n, kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, h->B.V, sizeof(double) * h->n, kind_from(ptr_kind), h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    return map_cuda(e);
+}
+
+int pic_set_particles(pic_handle* h, const double* r, const double* v, int ptr_kind) {
+    if (!h || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    if (h->n == 0) return PIC_OK;
+    if (!r || !v) return PIC_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(h->B.R, r, sizeof(double) * h->n, kind_to(ptr_kind), h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.V, v, sizeof(double) * h->n, kind_to(ptr_kind), h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    return map_cuda(e);
+}
+
+int pic_get_periods(pic_handle* h, double* T, int64_t* N, double* o, int ptr_kind) {
+    if (!h || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    if (h->n == 0) return PIC_OK;
+    const size_t n = (size_t)h->n;
+    cudaError_t e = cudaSuccess;
+    double *dT = T, *dO = o;
+    long long* dN = (long long*)N;
+    void* tmp = nullptr;
+    if (ptr_kind == PIC_PTR_HOST) {
+        e = cudaMallocAsync(&tmp, n * (2 * sizeof(double) + sizeof(long long)), h->st);
+        if (e != cudaSuccess) return map_cuda(e);
+        dT = T ? (double*)tmp : nullptr;
+        dO = o ? (double*)tmp + n : nullptr;
+        dN = N ? (long long*)((double*)tmp + 2 * n) : nullptr;
+    }
+    long long want = ((long long)n + 255) / 256;
+    int grid = (int)(want < (long long)h->sm_count * 4 ? want : (long long)h->sm_count * 4);
+    k_export_periods<<<grid, 256, 0, h->st>>>(h->n, h->dp.h, h->B.T, h->B.N, h->B.o, dT, dN, dO);
+    ++h->launches;
+    e = cudaGetLastError();
+    if (ptr_kind == PIC_PTR_HOST) {
+        if (e == cudaSuccess && T) e = cudaMemcpyAsync(T, dT, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess && o) e = cudaMemcpyAsync(o, dO, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess && N) e = cudaMemcpyAsync(N, dN, n * sizeof(long long), cudaMemcpyDeviceToHost, h->st);
+        cudaError_t e2 = cudaFreeAsync(tmp, h->st);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    return map_cuda(e);
+}
+
+int pic_get_state(pic_handle* h, pic_state_t* out) {
+    if (!h || !out) return PIC_ERR_INVALID_ARG;
+    out->t = h->t;
+    out->n_steps = h->n_steps;
+    if (h->n == 0) return PIC_OK;
+    if (!out->r || !out->v || !out->T) return PIC_ERR_INVALID_ARG;
+    const size_t n = (size_t)h->n;
+    cudaError_t e = cudaMemcpyAsync(out->r, h->B.R, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->v, h->B.V, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    const double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->T, Ts, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    return map_cuda(e);
+}
+
+int pic_set_state(pic_handle* h, const pic_state_t* in) {
+    if (!h || !in) return PIC_ERR_INVALID_ARG;
+    if (h->n > 0 && (!in->r || !in->v || !in->T)) return PIC_ERR_INVALID_ARG;
+    if (in->n_steps < 0) return PIC_ERR_INVALID_ARG;
+    const size_t n = (size_t)h->n;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(h->B.R, in->r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.V, in->v, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Ts, in->T, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    }
+    if (e != cudaSuccess) return map_cuda(e);
+    h->t = in->t;
+    h->n_steps = in->n_steps;
+    return PIC_OK;
+}
+
+int64_t pic_num_particles(const pic_handle* h) { return h ? h->n : -1; }
+
+int64_t pic_launch_count(const pic_handle* h) { return h ? h->launches : -1; }
+
+void pic_destroy(pic_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+}
+
+// ---------------------------------------------------------- standalone mesh
+
+int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_dev, int64_t* n_out_dev,
+                void* stream) {
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !R_dev) || !Q_dev || !n_out_dev) return PIC_ERR_INVALID_ARG;
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+    DevParams d;
+    make_devparams(p, n, &d);
+    return map_cuda(pic::launch_deposit(d, R_dev, n, (long long*)Q_dev, (long long*)n_out_dev,
+                                        (cudaStream_t)stream, sms, nullptr));
+}
+
+int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                double* rE_edges_dev, void* stream) {
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
+    if ((double)n_particles * (double)p->weight_fixed >= 4.611686018427388e18) return PIC_ERR_OVERFLOW;
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+    DevParams d;
+    make_devparams(p, n_particles, &d);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tiles = (p->n_cells + pic::kScanTile - 1) / pic::kScanTile;
+    const size_t bytes = pic::scan_scratch_layout(p->n_cells, tiles, nullptr, nullptr);
+    void* mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, bytes, st);
+    if (e != cudaSuccess) return map_cuda(e);
+    pic::ScanScratch S;
+    pic::scan_scratch_layout(p->n_cells, tiles, mem, &S);
+    int status = 0;
+    e = pic::launch_poisson(d, (const long long*)Q_dev, E_dev, rE_edges_dev, S, st, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, S.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaFreeAsync(mem, st);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_cuda(e);
+    return map_dev(status);
+}
+
+int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double* E_dev,
+               const double* rE_edges_dev, double* e_dev, void* stream) {
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!R_dev || !e_dev)) || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+    DevParams d;
+    make_devparams(p, n, &d);
+    return map_cuda(pic::launch_gather(d, R_dev, n, E_dev, rE_edges_dev, e_dev, (cudaStream_t)stream, sms, nullptr));
+}
+
+// Testing hook: a Poisson window whose grid barrier waits for one arrival
+// that never comes, with the given limit; returns the status pic_step gives.
+int pic_test_barrier_timeout(int64_t wait_limit_ns, void* stream) {
+    if (wait_limit_ns <= 0 || wait_limit_ns > 10000000000ll) return PIC_ERR_INVALID_ARG;
+    pic_params p;
+    pic_default_params(&p);
+    p.wait_limit_ns = wait_limit_ns;
+    p.block_size = 128;
+    std::vector<double> r(256), v(256);
+    for (int i = 0; i < 256; ++i) {
+        r[i] = -1.0 + 2.0 * (i + 0.5) / 256.0;
+        v[i] = 0.5;
+    }
+    pic_handle* h = nullptr;
+    int rc = pic_init(&p, 256, r.data(), v.data(), PIC_PTR_HOST, stream, &h);
+    if (rc) return rc;
+    h->dp.bar_extra = 1;
+    rc = pic_step(h, 1);
+    pic_destroy(h);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,275 @@
+// mesh.cu -- standalone field-cycle kernels: CIC deposit, trapezoid prefix
+// integral (decoupled look-back int64 scan) and gather (Sec. 2.3 of Frenod,
+// Hirstoaga & Lutz; eq. VlasPoissAxSymBeam).
+#include "pic_device.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+// ------------------------------------------------------------------ deposit
+
+// Linear deposit of every particle as exact integers: floor(f W) units to
+// the right node, W - floor(f W) to the left one.  Per-block histogram in
+// shared memory when it fits, flushed with 64-bit integer atomics, so the
+// result does not depend on the order of the additions.
+__global__ void k_deposit(DevParams P, const double* __restrict__ R, long long n,
+                          unsigned long long* __restrict__ Q, unsigned long long* __restrict__ n_out,
+                          int use_smem) {
+    extern __shared__ unsigned long long hist[];
+    const int Np1 = P.n_cells + 1;
+    if (use_smem) {
+        for (int j = threadIdx.x; j < Np1; j += blockDim.x) hist[j] = 0ull;
+        __syncthreads();
+    }
+    unsigned long long* H = use_smem ? hist : Q;
+    unsigned int out = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Cell c = mesh_locate(P, R[i]);
+        if (c.j >= 0) {
+            atomicAdd(&H[c.j], (unsigned long long)(P.W - c.qR));
+            if (c.qR) atomicAdd(&H[c.j + 1], (unsigned long long)c.qR);
+        } else {
+            ++out;
+        }
+    }
+    out = __reduce_add_sync(0xffffffffu, out);
+    if ((threadIdx.x & 31) == 0 && out) atomicAdd(n_out, (unsigned long long)out);
+    if (use_smem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < Np1; j += blockDim.x) {
+            unsigned long long v = hist[j];
+            if (v) atomicAdd(&Q[j], v);
+        }
+    }
+}
+
+// ------------------------------------------------- decoupled look-back scan
+
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ long long warp_incl_scan(long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+
+// G_j = sum_{m<j} (Q_m + Q_{m+1}), j = 0..n_cells, in one pass: each block
+// scans a tile with warp shuffles, then its first thread looks back over
+// the published aggregates/prefixes of earlier tiles (tiles are taken in
+// launch order through an atomic counter, so every tile it waits on is
+// already running).  Each wait has a time limit that sets the status word.
+__global__ void __launch_bounds__(kScanThreads) k_scan_pairs(DevParams P, const long long* __restrict__ Q,
+                                                             ScanScratch S) {
+    __shared__ int s_tile;
+    __shared__ long long s_warp[kScanThreads / 32];
+    __shared__ long long s_excl;
+    const int Nc = P.n_cells;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(S.tile_ctr, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long long m = base + k;
+        v[k] = (m < Nc) ? Q[m] + Q[m + 1] : 0;
+        sum += v[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = warp_incl_scan(sum);
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        long long y = (lane < kScanThreads / 32) ? s_warp[lane] : 0;
+        y = warp_incl_scan(y);
+        if (lane < kScanThreads / 32) s_warp[lane] = y;
+    }
+    __syncthreads();
+    const long long total = s_warp[kScanThreads / 32 - 1];
+    const long long in_block = incl - sum + (w > 0 ? s_warp[w - 1] : 0);
+    if (threadIdx.x == 0) {
+        long long excl = 0;
+        if (tile == 0) {
+            S.incl[0] = total;
+            st_release_s32(&S.flag[0], 2);
+        } else {
+            S.agg[tile] = total;
+            st_release_s32(&S.flag[tile], 1);
+            int p = tile - 1;
+            long long t0 = 0;
+            unsigned spins = 0;
+            while (p >= 0) {
+                int f = ld_acquire_s32(&S.flag[p]);
+                if (f == 2) {
+                    excl += __ldcg(&S.incl[p]);
+                    break;
+                }
+                if (f == 1) {
+                    excl += __ldcg(&S.agg[p]);
+                    --p;
+                    continue;
+                }
+                if ((++spins & 63) == 0) {
+                    long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > P.wait_ns) {
+                        atomicCAS(S.status, 0, (int)DEV_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            S.incl[tile] = excl + total;
+            st_release_s32(&S.flag[tile], 2);
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    long long run = s_excl + in_block;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long long m = base + k;
+        if (m < Nc) {
+            S.G[m] = run;
+            if (m == Nc - 1) S.G[Nc] = run + v[k];
+        }
+        run += v[k];
+    }
+}
+
+// S_j = G_j - G_c (the integral from r = 0), rE_j = S_j q_unit/2,
+// E_j = rE_j * (1/r_j); at r = 0, E = rho(0) = Q_c q_unit / h_r.
+__global__ void k_field_from_prefix(DevParams P, const long long* __restrict__ Q,
+                                    const long long* __restrict__ G, double* __restrict__ E,
+                                    double* __restrict__ edges) {
+    const int Nc = P.n_cells, c = P.c;
+    const long long Gc = G[c];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= Nc; j += gridDim.x * blockDim.x) {
+        long long S = G[j] - Gc;
+        double e;
+        if (j == c) {
+            e = ((double)Q[c] * P.q_unit) * P.inv_hr;
+        } else {
+            double r = P.r_min + (double)j * P.hr;
+            e = ((double)S * P.q_half) * (1.0 / r);
+        }
+        E[j] = e;
+        if (j == 0) edges[0] = (double)S * P.q_half;
+        if (j == Nc) edges[1] = (double)S * P.q_half;
+    }
+}
+
+// ------------------------------------------------------------------ gather
+
+__global__ void k_gather(DevParams P, const double* __restrict__ R, long long n,
+                         const double* __restrict__ E, const double* __restrict__ edges,
+                         double* __restrict__ out, int use_smem) {
+    extern __shared__ double2 tab[];
+    const int Nc = P.n_cells;
+    if (use_smem) {
+        for (int j = threadIdx.x; j < Nc; j += blockDim.x)
+            tab[j] = make_double2(E[j], (E[j + 1] - E[j]) * P.invW);
+        __syncthreads();
+    }
+    const double lo = edges[0], hi = edges[1];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Cell c = mesh_locate(P, R[i]);
+        double e;
+        if (use_smem) {
+            e = mesh_gather(tab, lo, hi, c.j, c.a);
+        } else if (c.j >= 0) {
+            double ej = E[c.j];
+            e = fma(c.a, (E[c.j + 1] - ej) * P.invW, ej);
+        } else {
+            e = (c.j == -1 ? lo : hi) / c.a;
+        }
+        out[i] = e;
+    }
+}
+
+// ------------------------------------------------------------ host launchers
+
+cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, long long* Q,
+                           long long* n_out, cudaStream_t st, int sm_count, long long* launches) {
+    const int Np1 = P.n_cells + 1;
+    cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(long long) * (size_t)Np1, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_out, 0, sizeof(long long), st);
+    if (e != cudaSuccess || n == 0) return e;
+    size_t smem = sizeof(unsigned long long) * (size_t)Np1;
+    int use_smem = smem <= 96 * 1024;
+    if (use_smem && smem > 48 * 1024)
+        cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long long want = (n + 255) / 256;
+    int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
+    k_deposit<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, (unsigned long long*)Q,
+                                                      (unsigned long long*)n_out, use_smem);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+size_t scan_scratch_bytes(int n_cells) {
+    const int tiles = (n_cells + kScanTile - 1) / kScanTile;
+    return scan_scratch_layout(n_cells, tiles, nullptr, nullptr);
+}
+
+size_t scan_scratch_layout(int n_cells, int tiles, void* base, ScanScratch* S) {
+    // agg, incl (tiles int64 each), G (n_cells+1 int64), flag (tiles int32),
+    // tile counter and status (int32 each); every piece 256-byte aligned.
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off_agg = 0;
+    size_t off_incl = up(off_agg + sizeof(long long) * tiles);
+    size_t off_G = up(off_incl + sizeof(long long) * tiles);
+    size_t off_flag = up(off_G + sizeof(long long) * (size_t)(n_cells + 1));
+    size_t off_ctr = up(off_flag + sizeof(int) * tiles);
+    size_t off_status = up(off_ctr + sizeof(unsigned int));
+    size_t total = up(off_status + sizeof(int));
+    if (S && base) {
+        char* b = (char*)base;
+        S->agg = (long long*)(b + off_agg);
+        S->incl = (long long*)(b + off_incl);
+        S->G = (long long*)(b + off_G);
+        S->flag = (int*)(b + off_flag);
+        S->tile_ctr = (unsigned int*)(b + off_ctr);
+        S->status = (int*)(b + off_status);
+        S->zero_from = off_flag;  // flags, counter and status must start at zero
+        S->zero_bytes = total - off_flag;
+    }
+    return total;
+}
+
+cudaError_t launch_poisson(const DevParams& P, const long long* Q, double* E, double* edges,
+                           const ScanScratch& S, cudaStream_t st, long long* launches) {
+    const int tiles = (P.n_cells + kScanTile - 1) / kScanTile;
+    cudaError_t e = cudaMemsetAsync((char*)S.flag, 0, S.zero_bytes, st);
+    if (e != cudaSuccess) return e;
+    k_scan_pairs<<<tiles, kScanThreads, 0, st>>>(P, Q, S);
+    int fgrid = (P.n_cells + 1 + 255) / 256;
+    k_field_from_prefix<<<fgrid, 256, 0, st>>>(P, Q, S.G, E, edges);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DevParams& P, const double* R, long long n, const double* E,
+                          const double* edges, double* out, cudaStream_t st, int sm_count,
+                          long long* launches) {
+    if (n == 0) return cudaSuccess;
+    size_t smem = sizeof(double2) * (size_t)P.n_cells;
+    int use_smem = smem <= 96 * 1024;
+    if (use_smem && smem > 48 * 1024)
+        cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long long want = (n + 255) / 256;
+    int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
+    k_gather<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, E, edges, out, use_smem);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,79 @@
+// pic_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Device scratch of the decoupled look-back scan.
+struct ScanScratch {
+    long long* agg;          // per tile: aggregate
+    long long* incl;         // per tile: inclusive prefix
+    long long* G;            // n_cells+1: exclusive prefix of Q_m + Q_{m+1}
+    int* flag;               // per tile: 0 none, 1 aggregate, 2 prefix
+    unsigned int* tile_ctr;  // dynamic tile index
+    int* status;             // DEV_* of the launch
+    size_t zero_from, zero_bytes;
+};
+
+size_t scan_scratch_bytes(int n_cells);
+size_t scan_scratch_layout(int n_cells, int tiles, void* base, ScanScratch* S);
+
+cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, long long* Q,
+                           long long* n_out, cudaStream_t st, int sm_count, long long* launches);
+cudaError_t launch_poisson(const DevParams& P, const long long* Q, double* E, double* edges,
+                           const ScanScratch& S, cudaStream_t st, long long* launches);
+cudaError_t launch_gather(const DevParams& P, const double* R, long long n, const double* E,
+                          const double* edges, double* out, cudaStream_t st, int sm_count,
+                          long long* launches);
+
+// Per-particle device state of a window (structure of arrays, n entries each
+// unless stated).
+struct WinBufs {
+    double *R, *V;              // current fine sample y_k
+    double* Vm2;                // V_{k-1} carried to the next sample
+    double *t1, *T, *o;         // first extremum, period, remainder (fine steps)
+    int *N, *need, *flags;      // whole periods, last sample needed, Track flags
+    double *c0, *c1, *c2, *c3, *c4, *c5;  // stage values carried across a field cycle
+    int *j0, *j1;               // cells carried across a field cycle
+    double2* traj;              // (Kmax+1) rows of n samples (R, V)
+    unsigned long long* Qring;  // 3 cycles x 2 fields x (n_cells+1)
+    int* notdone;               // 3 cycles
+    unsigned int* bar;          // grid barrier arrivals
+    int* status;                // DEV_* of the launch
+    long long* K_out;           // fine steps of the window
+};
+
+enum WindowMode { MODE_PERIODS = 0, MODE_ETD = 1, MODE_FINE = 2 };
+
+struct WindowLaunch {
+    int coop_grid = 0, coop_block = 0;
+    size_t coop_smem = 0;
+};
+
+cudaError_t window_prepare(const DevParams& P, int block, int sm_count, WindowLaunch* L);
+// Poisson: one cooperative persistent launch per macro step (or per fine run).
+cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L,
+                               int mode, int T_known, long long n_fine, cudaStream_t st,
+                               long long* launches, const double* Tin);
+// Duffing / zero field: one thread per particle, all n_macro macro steps in
+// one launch (no coupling between particles).
+cudaError_t launch_window_local(const DevParams& P, const WinBufs& B, int mode, int T_known,
+                                long long n_iter, int block, int sm_count, cudaStream_t st,
+                                long long* launches, const double* Tin);
+
+// Reductions for pic_moments: per-block partial sums, combined on the host
+// in a fixed order.
+constexpr int kMomDoubles = 8;   // sumR sumV sumR2 sumV2 sumR4 sumT minT maxT
+constexpr int kMomInts = 3;      // minN maxN n_fallback
+cudaError_t launch_moments(const DevParams& P, const WinBufs& B, double* part_d,
+                           long long* part_i, int grid, cudaStream_t st, long long* launches);
+
+}  // namespace pic

@@ -1,0 +1,654 @@
+// window.cu -- the fine window of Algorithm ETDFSSModAlgo (Frenod, Hirstoaga
+// & Lutz, Sec. 3): fine solver from y^n with period detection (Remark
+// CompOfThePeriodsRem), quadratic landing at o and o+T (Remark
+// QuadraticInterpolationRem) and the N-turn extrapolation (eq. MainFormula1).
+//
+// Self-consistent Poisson field: one cooperative persistent launch per macro
+// step.  Each fine stage needs the field of every particle's stage position
+// (Sec. 3: all particles are pushed far enough "to calculate the correct
+// self-consistent electric field").  Because E enters only dV/dt, the
+// R-component of stage s depends on fields of stages <= s-2, so stages pair
+// up: RK4 deposits stages (1,2) then (3,4); Lawson RK4 deposits (1,3) then
+// (2,4).  One fine step is therefore two field cycles:
+//   sweep: gather previous pair, advance, deposit the next pair into a
+//          shared-memory int64 histogram per block;
+//   flush the histograms with global int64 atomics; grid barrier;
+//   every block scans the mesh charge (block-wide int64 scan) into its own
+//   shared-memory field table.
+// Histogram sets rotate over three buffers so one barrier per cycle suffices.
+#include "pic_internal.h"
+
+namespace pic {
+
+constexpr int kWinMaxThreads = 1024;
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ void deposit_cell(unsigned long long* h, const Cell& c, long long W) {
+    if (c.j >= 0) {
+        atomicAdd(&h[c.j], (unsigned long long)(W - c.qR));
+        if (c.qR) atomicAdd(&h[c.j + 1], (unsigned long long)c.qR);
+    }
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    return x;
+}
+
+// g_j = sum_{m<j} (q_m + q_{m+1}), j = 0..Nc (block-wide, shared memory).
+__device__ void block_exscan_pairs(const long long* q, long long* g, int Nc, long long* s_warp) {
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
+    const int per = (Nc + T - 1) / T;
+    const int beg = min(t * per, Nc), end = min(beg + per, Nc);
+    long long s = 0;
+    for (int m = beg; m < end; ++m) s += q[m] + q[m + 1];
+    long long x = warp_incl_scan64(s);
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long y = (lane < nw) ? s_warp[lane] : 0;
+        y = warp_incl_scan64(y);
+        if (lane < nw) s_warp[lane] = y;
+    }
+    __syncthreads();
+    long long run = x - s + (w > 0 ? s_warp[w - 1] : 0);
+    for (int m = beg; m < end; ++m) {
+        g[m] = run;
+        run += q[m] + q[m + 1];
+    }
+    if (end == Nc && beg < end) g[Nc] = run;
+    __syncthreads();
+}
+
+// Field tables of one cycle (two fields) from the cycle's global charge:
+// trapezoid integral from r = 0 (S_j = g_j - g_c), E_j = S_j q_unit/2 * (1/r_j),
+// E_c = Q_c q_unit / h_r, then (E_j, (E_{j+1}-E_j)/W) per cell.
+__device__ void build_fields(const DevParams& P, const unsigned long long* Qg, long long* q,
+                             long long* g, double2* tab, const double* inv_r, double* edges,
+                             long long* s_warp) {
+    const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
+    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + idx);
+    __syncthreads();
+    block_exscan_pairs(q, g, Nc, s_warp);
+    block_exscan_pairs(q + Np1, g + Np1, Nc, s_warp);
+    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
+        const int f = idx >= Np1, j = idx - f * Np1;
+        const long long S = g[idx] - g[f * Np1 + c];
+        double e;
+        if (j == c) e = ((double)q[f * Np1 + c] * P.q_unit) * P.inv_hr;
+        else e = ((double)S * P.q_half) * inv_r[j];
+        tab[idx].x = e;
+        if (j == 0) edges[2 * f] = (double)S * P.q_half;
+        if (j == Nc) edges[2 * f + 1] = (double)S * P.q_half;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
+        const int f = idx >= Np1, j = idx - f * Np1;
+        tab[idx].y = (j < Nc) ? (tab[idx + 1].x - tab[idx].x) * P.invW : 0.0;
+    }
+    __syncthreads();
+}
+
+// Grid barrier with a time limit; false if any block timed out or failed.
+__device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& target,
+                                          int* status, int* s_ok) {
+    __syncthreads();
+    target += gridDim.x + P.bar_extra;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        long long t0 = 0;
+        unsigned spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if ((++spins & 31) == 0) {
+                if (ld_acquire_s32(status) != 0) {
+                    ok = 0;
+                    break;
+                }
+                long long now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > P.wait_ns) {
+                    atomicCAS(status, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Period tracking of one particle at sample k (k >= 1), with lazy loads of
+// the rarely used fields.  Returns true when the particle is done.
+__device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& B, long long i, int k,
+                                             double Vold, double Vnew, bool detect_only) {
+    int fl = B.flags[i];
+    if (!(fl & F_RES)) {
+        Track s;
+        s.flags = fl;
+        s.t1 = 0.0;
+        bool touched = false;
+        if (k >= 2) {
+            double v0 = B.Vm2[i];
+            if ((v0 > 0.0) != (Vold > 0.0)) {
+                if ((fl & F_NEXT) >= 1) s.t1 = B.t1[i];
+                track_sample(s, P, k, v0, Vold, Vnew, detect_only);
+                touched = true;
+            }
+        }
+        if (k == P.Kmax) {
+            track_cap(s, P, detect_only);
+            touched = true;
+        }
+        if (touched) {
+            B.flags[i] = s.flags;
+            if ((s.flags & F_NEXT) == 1 && !(fl & F_NEXT)) B.t1[i] = s.t1;
+            if (s.flags & F_RES) {
+                B.T[i] = s.T;
+                if (!detect_only) {
+                    B.o[i] = s.o;
+                    B.N[i] = s.N;
+                    B.need[i] = s.need;
+                }
+            }
+            fl = s.flags;
+        }
+        if (!(fl & F_RES)) B.Vm2[i] = Vold;
+    }
+    if (!(fl & F_RES)) return false;
+    return detect_only || k >= B.need[i];
+}
+
+// ------------------------------------------------ cooperative Poisson window
+
+template <int SOLVER>
+__global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, WinBufs B, int mode, int T_known,
+                                                                long long n_fine, const double* __restrict__ Tin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Nc = P.n_cells, Np1 = Nc + 1;
+    double2* tab = (double2*)smem_raw;                                   // 2 Np1
+    unsigned long long* hist = (unsigned long long*)(tab + 2 * Np1);      // 2 Np1 (scan input too)
+    long long* g = (long long*)(hist + 2 * Np1);                          // 2 Np1
+    double* inv_r = (double*)(g + 2 * Np1);                               // Np1
+    __shared__ double s_edges[4];
+    __shared__ long long s_warp[32];
+    __shared__ int s_ok, s_cnt, s_stop;
+
+    for (int j = threadIdx.x; j < Np1; j += blockDim.x)
+        inv_r[j] = (j == P.c) ? 0.0 : 1.0 / (P.r_min + (double)j * P.hr);
+
+    const bool detect_only = mode == MODE_PERIODS, fine_only = mode == MODE_FINE;
+    const long long n = P.n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const double ie = P.inv_eps, mie = P.mie;
+    const long long W = P.W;
+    unsigned int target = 0;
+    int cyc = 0;
+    int K = 0;
+
+    if (!fine_only) {
+        for (long long i = i0; i < n; i += stride) {
+            if (T_known) {
+                Track s;
+                s.flags = 0;
+                s.t1 = 0.0;
+                track_resolve(s, P, Tin[i]);
+                B.T[i] = s.T;
+                B.o[i] = s.o;
+                B.N[i] = s.N;
+                B.need[i] = s.need;
+                B.flags[i] = s.flags;
+            } else {
+                B.flags[i] = 0;
+            }
+        }
+    }
+
+    for (int k = 0;; ++k) {
+        // ---- sweep A(k): finish step k-1, sample k, deposit stage pair 1 of step k
+        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) hist[idx] = 0ull;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const bool last_fine = fine_only && k == n_fine;
+        unsigned int cnt = 0;
+        for (long long i = i0; i < n; i += stride) {
+            double R = B.R[i], V = B.V[i];
+            if (k > 0) {
+                double Rn, Vn;
+                if (SOLVER == 1) {
+                    const double e1 = B.c0[i], e3 = B.c1[i];
+                    const double e2 = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
+                    const double e4 = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
+                    const double A = fma(P.s1, V, P.c1 * R);
+                    const double Bv = fma(P.c1, V, -(P.s1 * R));
+                    const double e23 = e2 + e3;
+                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), A);
+                    Vn = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, e4)), Bv);
+                } else {
+                    const double pR = B.c0[i], pV = B.c1[i], R3 = B.c4[i], R4 = B.c5[i];
+                    const double e3 = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
+                    const double e4 = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
+                    const double k3V = fma(mie, R3, e3);
+                    const double V4 = fma(P.h, k3V, V);
+                    const double k4R = ie * V4, k4V = fma(mie, R4, e4);
+                    const double sR = pR + k4R;
+                    const double sV = (pV + 2.0 * k3V) + k4V;
+                    Rn = fma(P.h6, sR, R);
+                    Vn = fma(P.h6, sV, V);
+                }
+                bool done = true;
+                if (!fine_only) done = track_update(P, B, i, k, V, Vn, detect_only);
+                R = Rn;
+                V = Vn;
+                B.R[i] = R;
+                B.V[i] = V;
+                if (!fine_only) {
+                    if (!detect_only) {
+                        int fl = B.flags[i];
+                        if (!((fl & F_RES) && k > B.need[i])) B.traj[(size_t)k * n + i] = make_double2(R, V);
+                    }
+                    cnt += done ? 0u : 1u;
+                }
+            } else if (!fine_only) {
+                if (!detect_only) B.traj[i] = make_double2(R, V);
+                cnt += 1u;
+            }
+            if (last_fine) continue;
+            // stage pair 1
+            Cell ca, cb;
+            if (SOLVER == 1) {
+                ca = mesh_locate(P, R);                              // stage 1: y
+                cb = mesh_locate(P, fma(P.sh, V, P.ch * R));         // stage 3: Phi_h/2 y
+            } else {
+                ca = mesh_locate(P, R);                              // stage 1: y
+                const double R2 = fma(P.h2, ie * V, R);              // stage 2: y + h/2 k1
+                cb = mesh_locate(P, R2);
+                B.c4[i] = R2;
+            }
+            deposit_cell(hist, ca, W);
+            deposit_cell(hist + Np1, cb, W);
+            B.j0[i] = ca.j;
+            B.c2[i] = ca.a;
+            B.j1[i] = cb.j;
+            B.c3[i] = cb.a;
+        }
+        if (last_fine) break;
+        if (!fine_only) {
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, (int)cnt);
+        }
+        __syncthreads();
+        {
+            unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
+            for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
+                unsigned long long v = hist[idx];
+                if (v) atomicAdd(Qg + idx, v);
+            }
+            if (blockIdx.x == 0) {
+                unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
+                for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
+                if (threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
+            }
+            if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
+        }
+        if (!grid_sync(P, B.bar, target, B.status, &s_ok)) return;
+        if (!fine_only) {
+            if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
+            __syncthreads();
+            if (s_stop) {
+                K = k;
+                break;
+            }
+        }
+        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
+        ++cyc;
+
+        // ---- sweep B(k): gather pair 1, deposit stage pair 2
+        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) hist[idx] = 0ull;
+        __syncthreads();
+        for (long long i = i0; i < n; i += stride) {
+            const double R = B.R[i], V = B.V[i];
+            const double ea = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
+            const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
+            double Pa, Pb;
+            if (SOLVER == 1) {
+                // ea = e1 at y, eb = e3 at Phi_h/2 y
+                Pa = fma(P.sh, fma(P.h2, ea, V), P.ch * R);          // stage 2
+                Pb = fma(P.hsh, eb, fma(P.s1, V, P.c1 * R));         // stage 4
+                B.c0[i] = ea;
+                B.c1[i] = eb;
+            } else {
+                // ea = e1 at y, eb = e2 at y + h/2 k1
+                const double R2 = B.c4[i];
+                const double k1R = ie * V, k1V = fma(mie, R, ea);
+                const double V2 = fma(P.h2, k1V, V);
+                const double k2R = ie * V2, k2V = fma(mie, R2, eb);
+                const double R3 = fma(P.h2, k2R, R), V3 = fma(P.h2, k2V, V);
+                const double k3R = ie * V3;
+                const double R4 = fma(P.h, k3R, R);
+                Pa = R3;                                             // stage 3
+                Pb = R4;                                             // stage 4
+                B.c0[i] = (k1R + 2.0 * k2R) + 2.0 * k3R;
+                B.c1[i] = k1V + 2.0 * k2V;
+                B.c4[i] = R3;
+                B.c5[i] = R4;
+            }
+            const Cell ca = mesh_locate(P, Pa), cb = mesh_locate(P, Pb);
+            deposit_cell(hist, ca, W);
+            deposit_cell(hist + Np1, cb, W);
+            B.j0[i] = ca.j;
+            B.c2[i] = ca.a;
+            B.j1[i] = cb.j;
+            B.c3[i] = cb.a;
+        }
+        __syncthreads();
+        {
+            unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
+            for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
+                unsigned long long v = hist[idx];
+                if (v) atomicAdd(Qg + idx, v);
+            }
+            if (blockIdx.x == 0) {
+                unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
+                for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
+            }
+        }
+        if (!grid_sync(P, B.bar, target, B.status, &s_ok)) return;
+        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
+        ++cyc;
+    }
+
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !fine_only) *B.K_out = K;
+    if (mode != MODE_ETD) return;
+
+    // ---- landing (step 3) and extrapolation (step 4)
+    for (long long i = i0; i < n; i += stride) {
+        const double o = B.o[i], T = B.T[i];
+        const int N = B.N[i];
+        double y[2][2];
+        const int nt = N > 0 ? 2 : 1;
+        for (int t = 0; t < nt; ++t) {
+            const double u = t == 0 ? o : o + T;
+            const int kk = (int)floor(u);
+            const double sf = u - (double)kk;
+            const double2 a = B.traj[(size_t)kk * n + i];
+            const double2 b = B.traj[(size_t)(kk + 1) * n + i];
+            const double2 cc = B.traj[(size_t)(kk + 2) * n + i];
+            y[t][0] = interp3(a.x, b.x, cc.x, sf);
+            y[t][1] = interp3(a.y, b.y, cc.y, sf);
+        }
+        B.R[i] = extrapolate(y[0][0], y[nt - 1][0], N);
+        B.V[i] = extrapolate(y[0][1], y[nt - 1][1], N);
+    }
+}
+
+// ------------------------------------------- per-particle window (analytic E)
+
+template <int SOLVER, int FIELD>
+__device__ __forceinline__ void fine_step(const DevParams& P, double& R, double& V) {
+    if (SOLVER == 1) lawson_step_analytic(P, FIELD, R, V);
+    else rk4_step_analytic(P, FIELD, R, V);
+}
+
+template <int SOLVER, int FIELD>
+__global__ void __launch_bounds__(256) k_window_local(DevParams P, WinBufs B, int mode, int T_known,
+                                                      long long n_iter, const double* __restrict__ Tin) {
+    const long long n = P.n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int Kmax_seen = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double R = B.R[i], V = B.V[i];
+        if (mode == MODE_FINE) {
+            for (long long k = 0; k < n_iter; ++k) fine_step<SOLVER, FIELD>(P, R, V);
+            B.R[i] = R;
+            B.V[i] = V;
+            continue;
+        }
+        if (mode == MODE_PERIODS) {
+            Track s;
+            s.flags = 0;
+            s.t1 = 0.0;
+            s.T = 0.0;
+            double vkm2 = 0.0;
+            int K = 0;
+            for (;;) {
+                if (track_done(s, K, true)) break;
+                if (K == P.Kmax) {
+                    track_cap(s, P, true);
+                    break;
+                }
+                const double vkm1 = V;
+                fine_step<SOLVER, FIELD>(P, R, V);
+                ++K;
+                if (K >= 2) track_sample(s, P, K, vkm2, vkm1, V, true);
+                vkm2 = vkm1;
+            }
+            B.T[i] = s.T;
+            B.flags[i] = s.flags;
+            Kmax_seen = max(Kmax_seen, K);
+            continue;
+        }
+        // MODE_ETD: n_iter macro steps of this particle
+        Track base;
+        base.flags = 0;
+        base.t1 = 0.0;
+        if (T_known) track_resolve(base, P, Tin[i]);
+        Track s = base;
+        int K = 0;
+        for (long long m = 0; m < n_iter; ++m) {
+            double y[2][2];
+            if (T_known) {
+                // o, T and the stencils are known before the window starts
+                s = base;
+                const int k1 = (int)floor(s.o);
+                const int k2 = s.N > 0 ? (int)floor(s.o + s.T) : -10;
+                double a[3], b[3], c[3], d[3];
+                K = 0;
+                for (;;) {
+                    const int r1 = K - k1, r2 = K - k2;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (r1 == q) { a[q] = R; b[q] = V; }
+                        if (r2 == q) { c[q] = R; d[q] = V; }
+                    }
+                    if (K >= s.need) break;
+                    fine_step<SOLVER, FIELD>(P, R, V);
+                    ++K;
+                }
+                const double s1 = s.o - (double)k1;
+                y[0][0] = interp3(a[0], a[1], a[2], s1);
+                y[0][1] = interp3(b[0], b[1], b[2], s1);
+                if (s.N > 0) {
+                    const double s2 = (s.o + s.T) - (double)k2;
+                    y[1][0] = interp3(c[0], c[1], c[2], s2);
+                    y[1][1] = interp3(d[0], d[1], d[2], s2);
+                } else {
+                    y[1][0] = y[0][0];
+                    y[1][1] = y[0][1];
+                }
+            } else {
+                s.flags = 0;
+                s.t1 = 0.0;
+                double vkm2 = 0.0;
+                K = 0;
+                B.traj[i] = make_double2(R, V);
+                for (;;) {
+                    if (track_done(s, K, false)) break;
+                    if (K == P.Kmax) {
+                        track_cap(s, P, false);
+                        break;
+                    }
+                    const double vkm1 = V;
+                    fine_step<SOLVER, FIELD>(P, R, V);
+                    ++K;
+                    B.traj[(size_t)K * n + i] = make_double2(R, V);
+                    if (K >= 2) track_sample(s, P, K, vkm2, vkm1, V, false);
+                    vkm2 = vkm1;
+                }
+                const int nt = s.N > 0 ? 2 : 1;
+                for (int t = 0; t < nt; ++t) {
+                    const double u = t == 0 ? s.o : s.o + s.T;
+                    const int kk = (int)floor(u);
+                    const double sf = u - (double)kk;
+                    const double2 p0 = B.traj[(size_t)kk * n + i];
+                    const double2 p1 = B.traj[(size_t)(kk + 1) * n + i];
+                    const double2 p2 = B.traj[(size_t)(kk + 2) * n + i];
+                    y[t][0] = interp3(p0.x, p1.x, p2.x, sf);
+                    y[t][1] = interp3(p0.y, p1.y, p2.y, sf);
+                }
+                if (nt == 1) {
+                    y[1][0] = y[0][0];
+                    y[1][1] = y[0][1];
+                }
+            }
+            R = extrapolate(y[0][0], y[1][0], s.N);
+            V = extrapolate(y[0][1], y[1][1], s.N);
+            Kmax_seen = max(Kmax_seen, K);
+        }
+        B.R[i] = R;
+        B.V[i] = V;
+        if (n_iter > 0) {
+            B.T[i] = s.T;
+            B.o[i] = s.o;
+            B.N[i] = s.N;
+            B.flags[i] = s.flags;
+        }
+    }
+    Kmax_seen = __reduce_max_sync(0xffffffffu, (unsigned)Kmax_seen);
+    if ((threadIdx.x & 31) == 0 && Kmax_seen > 0) atomicMax((long long*)B.K_out, (long long)Kmax_seen);
+}
+
+// ------------------------------------------------------------- moments
+
+__global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* part_i) {
+    __shared__ double sd[32][kMomDoubles];
+    __shared__ long long si[32][kMomInts];
+    const long long n = P.n, stride = (long long)gridDim.x * blockDim.x;
+    double a[kMomDoubles] = {0, 0, 0, 0, 0, 0, INFINITY, -INFINITY};
+    long long b[kMomInts] = {LLONG_MAX, LLONG_MIN, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double R = B.R[i], V = B.V[i], T = B.T[i];
+        const double R2 = R * R;
+        a[0] += R;
+        a[1] += V;
+        a[2] += R2;
+        a[3] += V * V;
+        a[4] += R2 * R2;
+        a[5] += T;
+        a[6] = fmin(a[6], T);
+        a[7] = fmax(a[7], T);
+        const long long N = B.N[i];
+        b[0] = min(b[0], N);
+        b[1] = max(b[1], N);
+        b[2] += (B.flags[i] & F_FB) ? 1 : 0;
+    }
+    for (int d = 16; d >= 1; d >>= 1) {
+        for (int q = 0; q < 6; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], d);
+        a[6] = fmin(a[6], __shfl_xor_sync(0xffffffffu, a[6], d));
+        a[7] = fmax(a[7], __shfl_xor_sync(0xffffffffu, a[7], d));
+        b[0] = min(b[0], __shfl_xor_sync(0xffffffffu, b[0], d));
+        b[1] = max(b[1], __shfl_xor_sync(0xffffffffu, b[1], d));
+        b[2] += __shfl_xor_sync(0xffffffffu, b[2], d);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        for (int q = 0; q < kMomDoubles; ++q) sd[w][q] = a[q];
+        for (int q = 0; q < kMomInts; ++q) si[w][q] = b[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int v = 1; v < nw; ++v) {
+            for (int q = 0; q < 6; ++q) a[q] += sd[v][q];
+            a[6] = fmin(a[6], sd[v][6]);
+            a[7] = fmax(a[7], sd[v][7]);
+            b[0] = min(b[0], si[v][0]);
+            b[1] = max(b[1], si[v][1]);
+            b[2] += si[v][2];
+        }
+        for (int q = 0; q < kMomDoubles; ++q) part_d[(size_t)blockIdx.x * kMomDoubles + q] = a[q];
+        for (int q = 0; q < kMomInts; ++q) part_i[(size_t)blockIdx.x * kMomInts + q] = b[q];
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+static size_t coop_smem_bytes(int n_cells) {
+    const size_t Np1 = (size_t)n_cells + 1;
+    return 2 * Np1 * sizeof(double2) + 2 * Np1 * sizeof(unsigned long long) + 2 * Np1 * sizeof(long long) +
+           Np1 * sizeof(double);
+}
+
+template <int SOLVER>
+static cudaError_t prepare_one(int block, size_t smem, int* blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_window_coop<SOLVER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_window_coop<SOLVER>, block, smem);
+}
+
+cudaError_t window_prepare(const DevParams& P, int block, int sm_count, WindowLaunch* L) {
+    L->coop_block = block;
+    L->coop_smem = coop_smem_bytes(P.n_cells);
+    int b0 = 0, b1 = 0;
+    cudaError_t e = prepare_one<0>(block, L->coop_smem, &b0);
+    if (e == cudaSuccess) e = prepare_one<1>(block, L->coop_smem, &b1);
+    if (e != cudaSuccess) return e;
+    int bps = b0 < b1 ? b0 : b1;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    if (bps > 2) bps = 2;
+    long long need = (P.n + block - 1) / block;
+    long long grid = (long long)bps * sm_count;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    L->coop_grid = (int)grid;
+    return cudaSuccess;
+}
+
+cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L, int mode,
+                               int T_known, long long n_fine, cudaStream_t st, long long* launches,
+                               const double* Tin) {
+    void* fn = P.solver == 1 ? (void*)k_window_coop<1> : (void*)k_window_coop<0>;
+    DevParams Pc = P;
+    WinBufs Bc = B;
+    void* args[] = {&Pc, &Bc, &mode, &T_known, &n_fine, &Tin};
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(L.coop_grid), dim3(L.coop_block), args, L.coop_smem, st);
+    if (launches) ++*launches;
+    return e;
+}
+
+cudaError_t launch_window_local(const DevParams& P, const WinBufs& B, int mode, int T_known, long long n_iter,
+                                int block, int sm_count, cudaStream_t st, long long* launches,
+                                const double* Tin) {
+    long long want = (P.n + block - 1) / block;
+    long long cap = (long long)sm_count * 16;
+    int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    if (P.field == 1) {
+        if (P.solver == 1) k_window_local<1, 1><<<grid, block, 0, st>>>(P, B, mode, T_known, n_iter, Tin);
+        else k_window_local<0, 1><<<grid, block, 0, st>>>(P, B, mode, T_known, n_iter, Tin);
+    } else {
+        if (P.solver == 1) k_window_local<1, 2><<<grid, block, 0, st>>>(P, B, mode, T_known, n_iter, Tin);
+        else k_window_local<0, 2><<<grid, block, 0, st>>>(P, B, mode, T_known, n_iter, Tin);
+    }
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const DevParams& P, const WinBufs& B, double* part_d, long long* part_i, int grid,
+                           cudaStream_t st, long long* launches) {
+    k_moments<<<grid, 256, 0, st>>>(P, B, part_d, part_i);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace pic

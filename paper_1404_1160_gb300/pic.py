@@ -1,0 +1,313 @@
+"""Thin ctypes binding of the C ABI in include/pic.h (libpic.so).
+
+Every function here has the name of the C entry point it wraps and only
+marshals arguments: numpy arrays and CPU tensors are passed as host pointers,
+CUDA tensors as device pointers, torch streams as cudaStream_t.  All
+computation runs in the library's CUDA kernels; if libpic.so is missing or no
+CUDA device is usable, the calls raise instead of computing anything on the
+CPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK = 0
+PIC_ERR_INVALID_ARG = -1
+PIC_ERR_CUDA = -2
+PIC_ERR_TIMEOUT = -3
+PIC_ERR_OVERFLOW = -4
+PIC_ERR_UNSUPPORTED = -5
+PIC_ERR_NO_MEMORY = -6
+
+PIC_FIELD_POISSON, PIC_FIELD_DUFFING, PIC_FIELD_ZERO = 0, 1, 2
+PIC_FINE_RK4, PIC_FINE_LAWSON_RK4 = 0, 1
+PIC_PTR_HOST, PIC_PTR_DEVICE = 0, 1
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {pic_strerror(status)} (status {status})")
+
+
+class pic_params(C.Structure):
+    _fields_ = [
+        ("eps", C.c_double),
+        ("dt", C.c_double),
+        ("field_model", C.c_int32),
+        ("fine_solver", C.c_int32),
+        ("steps_per_turn", C.c_int32),
+        ("n_cells", C.c_int32),
+        ("r_min", C.c_double),
+        ("r_max", C.c_double),
+        ("total_charge", C.c_double),
+        ("weight_fixed", C.c_uint64),
+        ("max_window_steps", C.c_int32),
+        ("periods_once", C.c_int32),
+        ("precision", C.c_int32),
+        ("block_size", C.c_int32),
+        ("wait_limit_ns", C.c_int64),
+    ]
+
+
+class pic_moments_t(C.Structure):
+    _fields_ = [
+        ("t", C.c_double),
+        ("n_steps", C.c_int64),
+        ("n_particles", C.c_int64),
+        ("Q_total", C.c_int64),
+        ("n_out_of_mesh", C.c_int64),
+        ("charge", C.c_double),
+        ("kinetic", C.c_double),
+        ("duffing_energy", C.c_double),
+        ("mean_R", C.c_double),
+        ("mean_V", C.c_double),
+        ("rms_R", C.c_double),
+        ("rms_V", C.c_double),
+        ("T_min", C.c_double),
+        ("T_mean", C.c_double),
+        ("T_max", C.c_double),
+        ("N_min", C.c_int64),
+        ("N_max", C.c_int64),
+        ("window_steps", C.c_int64),
+        ("n_no_period", C.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pic_state_t(C.Structure):
+    _fields_ = [
+        ("r", C.POINTER(C.c_double)),
+        ("v", C.POINTER(C.c_double)),
+        ("T", C.POINTER(C.c_double)),
+        ("t", C.c_double),
+        ("n_steps", C.c_int64),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load() -> C.CDLL:
+    """Loads libpic.so (built by ``paper_1404_1160_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: run paper_1404_1160_gb300.build.build() (needs nvcc)")
+        lib = C.CDLL(LIB_PATH)
+        P, vp, i64, i32, d = C.POINTER, C.c_void_p, C.c_int64, C.c_int, C.c_double
+        H = vp  # opaque pic_handle*
+        sig = {
+            "pic_default_params": (None, [P(pic_params)]),
+            "pic_init": (i32, [P(pic_params), i64, vp, vp, i32, vp, P(H)]),
+            "pic_step": (i32, [H, i64]),
+            "pic_fine_steps": (i32, [H, i64]),
+            "pic_moments": (i32, [H, P(pic_moments_t)]),
+            "pic_get_particles": (i32, [H, vp, vp, i32]),
+            "pic_set_particles": (i32, [H, vp, vp, i32]),
+            "pic_get_periods": (i32, [H, vp, vp, vp, i32]),
+            "pic_get_field": (i32, [H, vp, vp, vp, vp, i32]),
+            "pic_get_state": (i32, [H, P(pic_state_t)]),
+            "pic_set_state": (i32, [H, P(pic_state_t)]),
+            "pic_num_particles": (i64, [H]),
+            "pic_launch_count": (i64, [H]),
+            "pic_destroy": (None, [H]),
+            "pic_strerror": (C.c_char_p, [i32]),
+            "pic_deposit": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
+            "pic_poisson": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
+            "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
+            "pic_test_barrier_timeout": (i32, [i64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------ marshalling
+
+
+def _ptr(x):
+    """(pointer, ptr_kind) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, PIC_PTR_HOST
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data, PIC_PTR_HOST
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (PIC_PTR_DEVICE if x.is_cuda else PIC_PTR_HOST)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _kind(*xs):
+    kinds = {_ptr(x)[1] for x in xs if x is not None}
+    if len(kinds) > 1:
+        raise ValueError("buffers of one call must all be host or all be device memory")
+    return kinds.pop() if kinds else PIC_PTR_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != PIC_OK:
+        raise PicError(rc, what)
+
+
+# ------------------------------------------------------------ entry points
+
+
+def pic_strerror(status: int) -> str:
+    return load().pic_strerror(status).decode()
+
+
+def pic_default_params(**overrides) -> pic_params:
+    p = pic_params()
+    load().pic_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owner of a pic_handle*; pic_destroy runs when it is closed or collected."""
+
+    def __init__(self, ptr: int, n: int):
+        self.ptr = C.c_void_p(ptr)
+        self.n = n
+
+    def close(self):
+        if self.ptr:
+            load().pic_destroy(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pic_init(params: pic_params, r0, v0, stream=None) -> Handle:
+    n = int(len(r0))
+    if len(v0) != n:
+        raise ValueError("r0 and v0 differ in length")
+    kind = _kind(r0, v0)
+    out = C.c_void_p()
+    _check(load().pic_init(C.byref(params), n, _ptr(r0)[0], _ptr(v0)[0], kind, _stream(stream), C.byref(out)), "pic_init")
+    return Handle(out.value, n)
+
+
+def pic_step(h: Handle, n_steps: int) -> None:
+    _check(load().pic_step(h.ptr, n_steps), "pic_step")
+
+
+def pic_fine_steps(h: Handle, n_fine: int) -> None:
+    _check(load().pic_fine_steps(h.ptr, n_fine), "pic_fine_steps")
+
+
+def pic_moments(h: Handle) -> dict:
+    m = pic_moments_t()
+    _check(load().pic_moments(h.ptr, C.byref(m)), "pic_moments")
+    return m.as_dict()
+
+
+def pic_get_particles(h: Handle, r=None, v=None):
+    """Fills r, v (host numpy by default) with the particle state."""
+    if r is None:
+        r = np.empty(h.n, np.float64)
+    if v is None:
+        v = np.empty(h.n, np.float64)
+    _check(load().pic_get_particles(h.ptr, _ptr(r)[0], _ptr(v)[0], _kind(r, v)), "pic_get_particles")
+    return r, v
+
+
+def pic_set_particles(h: Handle, r, v) -> None:
+    _check(load().pic_set_particles(h.ptr, _ptr(r)[0], _ptr(v)[0], _kind(r, v)), "pic_set_particles")
+
+
+def pic_get_periods(h: Handle):
+    T = np.empty(h.n, np.float64)
+    N = np.empty(h.n, np.int64)
+    o = np.empty(h.n, np.float64)
+    _check(load().pic_get_periods(h.ptr, _ptr(T)[0], _ptr(N)[0], _ptr(o)[0], PIC_PTR_HOST), "pic_get_periods")
+    return T, N, o
+
+
+def pic_get_field(h: Handle, n_cells: int):
+    Q = np.empty(n_cells + 1, np.int64)
+    E = np.empty(n_cells + 1, np.float64)
+    edges = np.empty(2, np.float64)
+    n_out = np.empty(1, np.int64)
+    _check(load().pic_get_field(h.ptr, _ptr(Q)[0], _ptr(E)[0], _ptr(edges)[0], _ptr(n_out)[0], PIC_PTR_HOST), "pic_get_field")
+    return Q, E, edges, int(n_out[0])
+
+
+def pic_get_state(h: Handle) -> dict:
+    r = np.empty(h.n, np.float64)
+    v = np.empty(h.n, np.float64)
+    T = np.empty(h.n, np.float64)
+    pd = C.POINTER(C.c_double)
+    st = pic_state_t(r.ctypes.data_as(pd), v.ctypes.data_as(pd), T.ctypes.data_as(pd), 0.0, 0)
+    _check(load().pic_get_state(h.ptr, C.byref(st)), "pic_get_state")
+    return {"r": r, "v": v, "T": T, "t": st.t, "n_steps": st.n_steps}
+
+
+def pic_set_state(h: Handle, state: dict) -> None:
+    r = np.ascontiguousarray(state["r"], np.float64)
+    v = np.ascontiguousarray(state["v"], np.float64)
+    T = np.ascontiguousarray(state["T"], np.float64)
+    pd = C.POINTER(C.c_double)
+    st = pic_state_t(r.ctypes.data_as(pd), v.ctypes.data_as(pd), T.ctypes.data_as(pd), float(state["t"]), int(state["n_steps"]))
+    _check(load().pic_set_state(h.ptr, C.byref(st)), "pic_set_state")
+
+
+def pic_num_particles(h: Handle) -> int:
+    return int(load().pic_num_particles(h.ptr))
+
+
+def pic_launch_count(h: Handle) -> int:
+    return int(load().pic_launch_count(h.ptr))
+
+
+def pic_destroy(h: Handle) -> None:
+    h.close()
+
+
+def pic_deposit(params: pic_params, R_dev, Q_dev, n_out_dev, stream=None) -> None:
+    _check(load().pic_deposit(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(Q_dev)[0], _ptr(n_out_dev)[0], _stream(stream)), "pic_deposit")
+
+
+def pic_poisson(params: pic_params, n_particles: int, Q_dev, E_dev, edges_dev, stream=None) -> None:
+    _check(load().pic_poisson(C.byref(params), n_particles, _ptr(Q_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _stream(stream)), "pic_poisson")
+
+
+def pic_gather(params: pic_params, R_dev, E_dev, edges_dev, e_dev, stream=None) -> None:
+    _check(load().pic_gather(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _ptr(e_dev)[0], _stream(stream)), "pic_gather")
+
+
+def pic_test_barrier_timeout(wait_limit_ns: int, stream=None) -> int:
+    """Returns the raw status (PIC_ERR_TIMEOUT expected)."""
+    return int(load().pic_test_barrier_timeout(wait_limit_ns, _stream(stream)))

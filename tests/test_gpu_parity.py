@@ -1,0 +1,318 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Integer work (the deposited charge) must match bit for bit.  Floating-point
+results must match within 1e-12 relative; the kernels evaluate the same
+IEEE operations in the same order as the oracle, so in practice they agree
+bit for bit and the tests also report that.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_1160_gb300 import inputs
+from paper_1404_1160_gb300 import pic
+from tests.gpu_common import assert_close, bit_equal, cfg_of
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_1160_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def mesh_positions(n, seed, r_max=4.0):
+    rng = np.random.default_rng(seed)
+    R = rng.normal(0, 1.2, n)
+    # edge cases: nodes, cell midpoints, mesh ends, outside, exactly r_max
+    extra = np.array([0.0, -r_max, r_max, r_max * (1 - 1e-16), -r_max * 1.5, r_max * 3, 1 / 32, -1 / 64, 3.999999999])
+    return np.concatenate([R, extra])
+
+
+# --------------------------------------------------------------- mesh kernels
+
+
+@pytest.mark.parametrize("n_cells,r_max,n", [(256, 4.0, 100_003), (1024, 4.0, 4097), (2, 1.0, 33), (65536, 8.0, 200_000)])
+def test_deposit_bit_exact(n_cells, r_max, n):
+    p = pic.pic_default_params(n_cells=n_cells, r_min=-r_max, r_max=r_max)
+    R = mesh_positions(n, seed=n_cells, r_max=r_max)
+    Q = torch.empty(n_cells + 1, dtype=torch.int64, device="cuda")
+    n_out = torch.empty(1, dtype=torch.int64, device="cuda")
+    pic.pic_deposit(p, dev(R), Q, n_out)
+    torch.cuda.synchronize()
+    Qo, no = oracle.deposit(cfg_of(p), R)
+    assert np.array_equal(Q.cpu().numpy(), Qo)
+    assert int(n_out.item()) == no
+    assert int(Qo.sum()) + no * p.weight_fixed == R.size * p.weight_fixed
+
+
+def test_deposit_empty_input():
+    p = pic.pic_default_params()
+    Q = torch.full((p.n_cells + 1,), 7, dtype=torch.int64, device="cuda")
+    n_out = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    pic.pic_deposit(p, torch.empty(0, dtype=torch.float64, device="cuda"), Q, n_out)
+    torch.cuda.synchronize()
+    assert int(Q.abs().sum()) == 0 and int(n_out.item()) == 0
+
+
+@pytest.mark.parametrize("n_cells", [2, 256, 1024, 2048, 4094, 65536])
+def test_poisson_bit_exact(n_cells):
+    # random charges span several scan tiles for the large meshes
+    rng = np.random.default_rng(n_cells)
+    p = pic.pic_default_params(n_cells=n_cells)
+    Q = rng.integers(0, 1 << 40, n_cells + 1).astype(np.int64)
+    n_particles = 10**6
+    E = torch.empty(n_cells + 1, dtype=torch.float64, device="cuda")
+    edges = torch.empty(2, dtype=torch.float64, device="cuda")
+    pic.pic_poisson(p, n_particles, dev(Q), E, edges)
+    S, Eo, edges_o = oracle.poisson(cfg_of(p), Q, n_particles)
+    assert bit_equal(E.cpu().numpy(), Eo)
+    assert bit_equal(edges.cpu().numpy(), edges_o)
+
+
+@pytest.mark.parametrize("n_cells,n", [(256, 123_457), (64, 31), (65536, 100_000)])
+def test_gather_bit_exact(n_cells, n):
+    p = pic.pic_default_params(n_cells=n_cells)
+    cfg = cfg_of(p)
+    R = mesh_positions(n, seed=5)
+    Q, _ = oracle.deposit(cfg, inputs.gaussian_beam(5000, seed=2, r_cut=4.0)[0])
+    _, E, edges = oracle.poisson(cfg, Q, 5000)
+    out = torch.empty(R.size, dtype=torch.float64, device="cuda")
+    pic.pic_gather(p, dev(R), dev(E), dev(edges), out)
+    torch.cuda.synchronize()
+    eo = oracle.gather(cfg, R, E, edges)
+    assert bit_equal(out.cpu().numpy(), eo)
+
+
+# --------------------------------------------------------------- fine solver
+
+
+@pytest.mark.parametrize("field", [pic.PIC_FIELD_POISSON, pic.PIC_FIELD_DUFFING, pic.PIC_FIELD_ZERO])
+@pytest.mark.parametrize("solver", [pic.PIC_FINE_RK4, pic.PIC_FINE_LAWSON_RK4])
+def test_fine_steps_match_oracle(field, solver):
+    p = pic.pic_default_params(field_model=field, fine_solver=solver)
+    R0, V0 = inputs.gaussian_beam(3001, seed=11, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_fine_steps(h, 7)
+    R, V = pic.pic_get_particles(h)
+    pic.pic_destroy(h)
+    Ro, Vo = oracle.fine_steps(cfg_of(p), R0, V0, 7)
+    assert_close(R, Ro, what="R")
+    assert_close(V, Vo, what="V")
+    assert bit_equal(R, Ro) and bit_equal(V, Vo)
+
+
+# -------------------------------------------------------- improved ETD step
+
+
+@pytest.mark.parametrize("solver", [pic.PIC_FINE_RK4, pic.PIC_FINE_LAWSON_RK4])
+@pytest.mark.parametrize("n", [1, 2000, 20_001])
+def test_etd_step_poisson_matches_oracle(solver, n):
+    # several blocks and a ragged tail; three macro steps with the
+    # self-consistent field
+    p = pic.pic_default_params(fine_solver=solver)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(n, seed=3, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    Ro, Vo = R0, V0
+    for step in range(3):
+        pic.pic_step(h, 1)
+        res = oracle.etd_step(cfg, Ro, Vo)
+        Ro, Vo = res.R, res.V
+        R, V = pic.pic_get_particles(h)
+        assert_close(R, Ro, what=f"R step {step}")
+        assert_close(V, Vo, what=f"V step {step}")
+        T, N, o = pic.pic_get_periods(h)
+        d = oracle.derive(cfg)
+        assert np.array_equal(N, res.N)
+        assert_close(T, res.T * d.h, what="T")
+        assert_close(o, res.o * d.h, what="o")
+        Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+        Qo, no = oracle.deposit(cfg, Ro)
+        assert np.array_equal(Q, Qo) and n_out == no
+        m = pic.pic_moments(h)
+        assert m["window_steps"] == res.stats["window_steps"]
+        assert m["n_no_period"] == res.stats["n_no_period"]
+    assert bit_equal(R, Ro) and bit_equal(V, Vo)
+    pic.pic_destroy(h)
+
+
+@pytest.mark.parametrize("solver", [pic.PIC_FINE_RK4, pic.PIC_FINE_LAWSON_RK4])
+def test_duffing_config0_shape_matches_oracle(solver):
+    # Duffing, eps 0.01, dt 0.05 (N = 0), periods once at init (Sec. 4.1)
+    p = pic.pic_default_params(field_model=pic.PIC_FIELD_DUFFING, dt=0.05, periods_once=1, fine_solver=solver)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(10_000, seed=0)
+    h = pic.pic_init(p, R0, V0)
+    st = pic.pic_get_state(h)
+    T, nf, _ = oracle.periods(cfg, R0, V0)
+    assert bit_equal(st["T"], T)
+    pic.pic_step(h, 20)
+    R, V = pic.pic_get_particles(h)
+    Ro, Vo = R0, V0
+    for _ in range(20):
+        res = oracle.etd_step(cfg, Ro, Vo, T)
+        Ro, Vo = res.R, res.V
+    assert np.all(res.N == 0)
+    assert_close(R, Ro, what="R")
+    assert_close(V, Vo, what="V")
+    assert bit_equal(R, Ro) and bit_equal(V, Vo)
+    pic.pic_destroy(h)
+
+
+@pytest.mark.parametrize("field", [pic.PIC_FIELD_DUFFING, pic.PIC_FIELD_ZERO])
+def test_local_field_periods_every_step(field):
+    # periods recomputed every macro step, dt = 0.5 (N about 8), with one
+    # particle at the equilibrium y = 0 of both fields (V never changes
+    # sign: 2 pi eps fallback, and y stays 0)
+    p = pic.pic_default_params(field_model=field, dt=0.5, periods_once=0)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(777, seed=4)
+    R0[0] = V0[0] = 0.0
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 3)
+    R, V = pic.pic_get_particles(h)
+    T, N, o = pic.pic_get_periods(h)
+    Ro, Vo = R0, V0
+    for _ in range(3):
+        res = oracle.etd_step(cfg, Ro, Vo)
+        Ro, Vo = res.R, res.V
+    assert R[0] == 0.0 and V[0] == 0.0
+    assert np.array_equal(N, res.N)
+    assert bit_equal(R, Ro) and bit_equal(V, Vo)
+    m = pic.pic_moments(h)
+    assert m["n_no_period"] == res.stats["n_no_period"] == 1
+    pic.pic_destroy(h)
+
+
+def test_out_of_mesh_particles_in_window():
+    # a few particles start beyond the mesh: they deposit nothing and feel
+    # rE_edge / R
+    p = pic.pic_default_params(r_min=-2.0, r_max=2.0, n_cells=128)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(3000, seed=9, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 2)
+    R, V = pic.pic_get_particles(h)
+    res = oracle.etd_step(cfg, R0, V0)
+    res = oracle.etd_step(cfg, res.R, res.V)
+    assert bit_equal(R, res.R) and bit_equal(V, res.V)
+    m = pic.pic_moments(h)
+    Qo, no = oracle.deposit(cfg, res.R)
+    assert no > 0 and m["n_out_of_mesh"] == no
+    assert m["Q_total"] + no * p.weight_fixed == 3000 * p.weight_fixed
+    pic.pic_destroy(h)
+
+
+def test_paper_workload_eps_1e_3():
+    # the paper's own run shape (Sec. 4.2): f0 of eq. InitialConditionBeam,
+    # eps = 1e-3, dt = 0.5, [-2, 2] with 256 cells
+    p = pic.pic_default_params(eps=1e-3, dt=0.5, r_min=-2.0, r_max=2.0)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.paper_beam(20000, seed=0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 1)
+    R, V = pic.pic_get_particles(h)
+    res = oracle.etd_step(cfg, R0, V0)
+    assert bit_equal(R, res.R) and bit_equal(V, res.V)
+    _, N, _ = pic.pic_get_periods(h)
+    assert np.array_equal(N, res.N) and N.min() >= 70
+    pic.pic_destroy(h)
+
+
+# -------------------------------------------------------- state and failures
+
+
+def test_checkpoint_resume_is_bit_identical():
+    p = pic.pic_default_params()
+    R0, V0 = inputs.gaussian_beam(5000, seed=12, r_cut=4.0)
+    a = pic.pic_init(p, R0, V0)
+    pic.pic_step(a, 4)
+    Ra, Va = pic.pic_get_particles(a)
+    b = pic.pic_init(p, R0, V0)
+    pic.pic_step(b, 2)
+    st = pic.pic_get_state(b)
+    pic.pic_destroy(b)
+    c = pic.pic_init(p, np.zeros(5000), np.zeros(5000))
+    pic.pic_set_state(c, st)
+    pic.pic_step(c, 2)
+    Rc, Vc = pic.pic_get_particles(c)
+    assert bit_equal(Ra, Rc) and bit_equal(Va, Vc)
+    assert pic.pic_moments(c)["n_steps"] == 4
+    pic.pic_destroy(a)
+    pic.pic_destroy(c)
+
+
+def test_empty_run():
+    p = pic.pic_default_params()
+    h = pic.pic_init(p, np.zeros(0), np.zeros(0))
+    pic.pic_step(h, 3)
+    m = pic.pic_moments(h)
+    assert m["n_particles"] == 0 and m["n_steps"] == 3
+    pic.pic_destroy(h)
+
+
+def test_barrier_wait_times_out_and_device_stays_usable():
+    # the barrier waits for an arrival that never comes: the kernel must
+    # give up after its limit and report PIC_ERR_TIMEOUT
+    rc = pic.pic_test_barrier_timeout(50_000_000)
+    assert rc == pic.PIC_ERR_TIMEOUT
+    p = pic.pic_default_params()
+    R0, V0 = inputs.gaussian_beam(1000, seed=1, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 1)
+    R, _ = pic.pic_get_particles(h)
+    assert bit_equal(R, oracle.etd_step(cfg_of(p), R0, V0).R)
+    pic.pic_destroy(h)
+
+
+def test_moments_match_numpy():
+    p = pic.pic_default_params(field_model=pic.PIC_FIELD_DUFFING, dt=0.05, periods_once=1)
+    R0, V0 = inputs.gaussian_beam(4096, seed=6)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 5)
+    R, V = pic.pic_get_particles(h)
+    m = pic.pic_moments(h)
+    w = 1.0 / R.size
+    assert m["mean_R"] == pytest.approx(R.mean(), rel=1e-12, abs=1e-15)
+    assert m["rms_V"] == pytest.approx(math.sqrt(np.mean(V * V)), rel=1e-12)
+    e2H = np.sum(w * (0.5 * (R * R + V * V) + 0.25 * p.eps * R**4))
+    assert m["duffing_energy"] == pytest.approx(e2H, rel=1e-12)
+    assert m["t"] == pytest.approx(5 * 0.05)
+    pic.pic_destroy(h)
+
+
+# -------------------------------------------------- full-size (bench) shape
+
+
+@pytest.mark.slow
+def test_full_size_vlasov_poisson_step_matches_oracle():
+    # the benchmark's workload: N_p = 1e6, eps 0.01, dt 0.1, 256 cells on
+    # [-4, 4], Lawson RK4, in the launch configuration bench.py times
+    p = pic.pic_default_params()
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(10**6, seed=0, r_cut=4.0)
+    h = pic.pic_init(p, dev(R0), dev(V0), torch.cuda.current_stream())
+    pic.pic_step(h, 1)
+    R, V = pic.pic_get_particles(h)
+    Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+    pic.pic_destroy(h)
+    res = oracle.etd_step(cfg, R0, V0)
+    Qo, no = oracle.deposit(cfg, res.R)
+    assert np.array_equal(Q, Qo) and n_out == no
+    assert int(Q.sum()) + n_out * p.weight_fixed == 10**6 * p.weight_fixed
+    assert_close(R, res.R, what="R")
+    assert_close(V, res.V, what="V")
+    assert bit_equal(R, res.R) and bit_equal(V, res.V)
