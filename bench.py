@@ -32,7 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/sec per GB300 (push+deposit+field) at stated error vs FP64 oracle"
 UNIT = "particle-steps/s"
-FP64_PEAK_FLOPS = 1.25e12  # nominal GB300 FP64 rate (no FP64 figure is measured by the driver)
+# FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x
+# 2.07 GHz = 1.258 TFLOP/s (GB300 nominal 1.25 TFLOP/s; a DFMA probe measured
+# 1.19 TFLOP/s at 2070 MHz).
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 
 WORKLOADS = {
     # paper-shaped Vlasov-Poisson run (the metric's workload)
@@ -120,7 +123,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     wl = WORKLOADS[args.workload]
-    n = wl["n"]
+    n = args.n_particles or wl["n"]
     # replicas: every rank advances its own beam (different seed)
     R0, V0 = inputs.gaussian_beam(n, seed=rank, r_cut=wl["r_cut"])
     prm = make_params(pic, args.workload)
@@ -184,7 +187,7 @@ def run_ours(args):
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
                     "kernel": "k_window_coop<1> (one launch per macro step)",
-                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived, not in MEASURED_PEAKS.json)",
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
                     "fine_steps_per_launch": K}
     else:
         roofline = None
@@ -288,11 +291,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="vp1e6")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--n-particles", type=int, default=0, help="override N_p (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -78,6 +78,8 @@ typedef struct {
                                   (the Duffing case of Sec. 4.1); 0: every step  */
     int32_t  precision;        /* 0 = FP64 (only value served)                    */
     int32_t  block_size;       /* CUDA threads per block, 0 = library default     */
+    int32_t  blocks_per_sm;    /* Poisson window blocks per SM, 0 = default (2)   */
+    int32_t  reserved;         /* must be 0                                       */
     int64_t  wait_limit_ns;    /* limit of every device-side wait, 0 = 2 s        */
 } pic_params;
 

@@ -42,6 +42,7 @@ int check_params(const pic_params* p, bool need_mesh) {
     if (p->precision != 0) return PIC_ERR_UNSUPPORTED;
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || (p->block_size & 31)))
         return PIC_ERR_INVALID_ARG;
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_ERR_INVALID_ARG;
     if (p->wait_limit_ns < 0) return PIC_ERR_INVALID_ARG;
     if (need_mesh || p->field_model == PIC_FIELD_POISSON) {
         if (p->n_cells < 2 || p->n_cells > 65536 || (p->n_cells & 1)) return PIC_ERR_INVALID_ARG;
@@ -93,6 +94,7 @@ void make_devparams(const pic_params* p, long long n, DevParams* d) {
     d->xs_scale = d->inv_hr * d->Wd;
     d->xs_off = -(p->r_min * d->inv_hr) * d->Wd;
     d->xs_max = (double)p->n_cells * d->Wd;
+    d->xs_max_i = (long long)p->n_cells * (long long)p->weight_fixed;
     d->q_unit = n > 0 ? p->total_charge / ((double)n * d->Wd) : 0.0;
     d->q_half = 0.5 * d->q_unit;
     d->field = p->field_model;
@@ -137,6 +139,7 @@ struct pic_handle {
     pic::WinBufs B;
     pic::WindowLaunch L;
     double* Tin = nullptr;   // periods of y^0 (fine steps) when periods_once
+    double *tmpR = nullptr, *tmpV = nullptr;  // unpacked R, V for copies in and out
     std::vector<void*> allocs;
     // field of the current positions
     long long *Qf = nullptr, *nout_f = nullptr;
@@ -187,7 +190,7 @@ cudaError_t reset_coop(pic_handle* h) {
     const size_t Np1 = (size_t)h->dp.n_cells + 1;
     cudaError_t e = cudaMemsetAsync(h->B.Qring, 0, sizeof(unsigned long long) * 3 * 2 * Np1, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.notdone, 0, sizeof(int) * 3, h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.bar, 0, sizeof(unsigned int), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.bar, 0, sizeof(unsigned int) * 64, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
     return e;
 }
@@ -285,26 +288,20 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     rc = PIC_OK;
 #define ALLOC(ptr, cnt) \
     if (!rc) rc = dalloc(h, &(ptr), (cnt))
-    ALLOC(B.R, N);
-    ALLOC(B.V, N);
+    ALLOC(B.y, N);
     ALLOC(B.Vm2, N);
     ALLOC(B.t1, N);
     ALLOC(B.T, N);
     ALLOC(B.o, N);
     ALLOC(B.N, N);
-    ALLOC(B.need, N);
-    ALLOC(B.flags, N);
+    ALLOC(B.tr, N);
+    ALLOC(h->tmpR, N);
+    ALLOC(h->tmpV, N);
     if (p->field_model == PIC_FIELD_POISSON) {
-        ALLOC(B.c0, N);
-        ALLOC(B.c1, N);
-        ALLOC(B.c2, N);
-        ALLOC(B.c3, N);
-        ALLOC(B.j0, N);
-        ALLOC(B.j1, N);
-        if (p->fine_solver == PIC_FINE_RK4) {
-            ALLOC(B.c4, N);
-            ALLOC(B.c5, N);
-        }
+        ALLOC(B.ce, N);
+        ALLOC(B.ca, N);
+        ALLOC(B.cx, N);
+        ALLOC(B.cj, N);
         ALLOC(B.Qring, 3 * 2 * Np1);
         ALLOC(h->Qf, Np1);
         ALLOC(h->nout_f, 1);
@@ -314,7 +311,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     if (need_traj) ALLOC(B.traj, ((size_t)p->max_window_steps + 1) * N);
     if (p->periods_once) ALLOC(h->Tin, N);
     ALLOC(B.notdone, 3);
-    ALLOC(B.bar, 1);
+    ALLOC(B.bar, 64);
     ALLOC(B.status, 1);
     ALLOC(B.K_out, 1);
 #undef ALLOC
@@ -339,16 +336,17 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
         rc = map_cuda(e);
     }
     if (!rc && n > 0) {
-        e = cudaMemcpyAsync(B.R, r0, sizeof(double) * N, kind_to(ptr_kind), h->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(B.V, v0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        e = cudaMemcpyAsync(h->tmpR, r0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, B.y, n, sms, h->st, &h->launches);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.T, 0, sizeof(double) * N, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.o, 0, sizeof(double) * N, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.N, 0, sizeof(int) * N, h->st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(B.flags, 0, sizeof(int) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.tr, 0, sizeof(int2) * N, h->st);
         rc = map_cuda(e);
     }
     if (!rc && p->field_model == PIC_FIELD_POISSON)
-        rc = map_cuda(pic::window_prepare(h->dp, h->block, sms, &h->L));
+        rc = map_cuda(pic::window_prepare(h->dp, h->block, p->blocks_per_sm, sms, &h->L));
     if (!rc && p->periods_once && n > 0) {
         // step 1 once, at initialisation (Sec. 4.1)
         rc = run_window(h, pic::MODE_PERIODS, 0);
@@ -390,7 +388,8 @@ int pic_get_field(pic_handle* h, int64_t* Q, double* E, double* rE_edges, int64_
     if (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE) return PIC_ERR_INVALID_ARG;
     if (h->n == 0) return PIC_ERR_INVALID_ARG;
     const size_t Np1 = (size_t)h->dp.n_cells + 1;
-    cudaError_t e = pic::launch_deposit(h->dp, h->B.R, h->n, h->Qf, h->nout_f, h->st, h->sm_count, &h->launches);
+    cudaError_t e = pic::launch_deposit(h->dp, (const double*)h->B.y, h->n, 2, h->Qf, h->nout_f, h->st, h->sm_count,
+                                        &h->launches);
     if (e == cudaSuccess) e = pic::launch_poisson(h->dp, h->Qf, h->Ef, h->edges_f, h->S, h->st, &h->launches);
     if (e == cudaSuccess && Q) e = cudaMemcpyAsync(Q, h->Qf, sizeof(long long) * Np1, kind_from(ptr_kind), h->st);
     if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, h->Ef, sizeof(double) * Np1, kind_from(ptr_kind), h->st);
@@ -467,9 +466,15 @@ int pic_moments(pic_handle* h, pic_moments_t* out) {
 int pic_get_particles(pic_handle* h, double* r, double* v, int ptr_kind) {
     if (!h || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
     if (h->n == 0) return PIC_OK;
-    cudaError_t e = cudaSuccess;
-    if (r) e = cudaMemcpyAsync(r, h->B.R, sizeof(double) * h->n, kind_from(ptr_kind), h->st);
-    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, h->B.V, sizeof(double) * h->n, kind_from(ptr_kind), h->st);
+    const size_t bytes = sizeof(double) * (size_t)h->n;
+    cudaError_t e;
+    if (ptr_kind == PIC_PTR_DEVICE) {
+        e = pic::launch_unpack(h->B.y, r, v, h->n, h->sm_count, h->st, &h->launches);
+    } else {
+        e = pic::launch_unpack(h->B.y, h->tmpR, h->tmpV, h->n, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess && r) e = cudaMemcpyAsync(r, h->tmpR, bytes, cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, h->tmpV, bytes, cudaMemcpyDeviceToHost, h->st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
 }
@@ -478,8 +483,10 @@ int pic_set_particles(pic_handle* h, const double* r, const double* v, int ptr_k
     if (!h || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
     if (h->n == 0) return PIC_OK;
     if (!r || !v) return PIC_ERR_INVALID_ARG;
-    cudaError_t e = cudaMemcpyAsync(h->B.R, r, sizeof(double) * h->n, kind_to(ptr_kind), h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.V, v, sizeof(double) * h->n, kind_to(ptr_kind), h->st);
+    const size_t bytes = sizeof(double) * (size_t)h->n;
+    cudaError_t e = cudaMemcpyAsync(h->tmpR, r, bytes, kind_to(ptr_kind), h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v, bytes, kind_to(ptr_kind), h->st);
+    if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, h->B.y, h->n, h->sm_count, h->st, &h->launches);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
 }
@@ -522,8 +529,9 @@ int pic_get_state(pic_handle* h, pic_state_t* out) {
     if (h->n == 0) return PIC_OK;
     if (!out->r || !out->v || !out->T) return PIC_ERR_INVALID_ARG;
     const size_t n = (size_t)h->n;
-    cudaError_t e = cudaMemcpyAsync(out->r, h->B.R, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->v, h->B.V, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e = pic::launch_unpack(h->B.y, h->tmpR, h->tmpV, h->n, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->r, h->tmpR, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->v, h->tmpV, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     const double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->T, Ts, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -537,8 +545,9 @@ int pic_set_state(pic_handle* h, const pic_state_t* in) {
     const size_t n = (size_t)h->n;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
-        e = cudaMemcpyAsync(h->B.R, in->r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->B.V, in->v, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        e = cudaMemcpyAsync(h->tmpR, in->r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, in->v, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, h->B.y, h->n, h->sm_count, h->st, &h->launches);
         double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
         if (e == cudaSuccess) e = cudaMemcpyAsync(Ts, in->T, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -571,7 +580,7 @@ int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_
     if ((rc = current_sm_count(&sms))) return rc;
     DevParams d;
     make_devparams(p, n, &d);
-    return map_cuda(pic::launch_deposit(d, R_dev, n, (long long*)Q_dev, (long long*)n_out_dev,
+    return map_cuda(pic::launch_deposit(d, R_dev, n, 1, (long long*)Q_dev, (long long*)n_out_dev,
                                         (cudaStream_t)stream, sms, nullptr));
 }
 

@@ -12,7 +12,8 @@ namespace pic {
 // the right node, W - floor(f W) to the left one.  Per-block histogram in
 // shared memory when it fits, flushed with 64-bit integer atomics, so the
 // result does not depend on the order of the additions.
-__global__ void k_deposit(DevParams P, const double* __restrict__ R, long long n,
+template <int POW2>
+__global__ void k_deposit(DevParams P, const double* __restrict__ R, long long n, int r_stride,
                           unsigned long long* __restrict__ Q, unsigned long long* __restrict__ n_out,
                           int use_smem) {
     extern __shared__ unsigned long long hist[];
@@ -25,7 +26,7 @@ __global__ void k_deposit(DevParams P, const double* __restrict__ R, long long n
     unsigned int out = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Cell c = mesh_locate(P, R[i]);
+        Cell c = mesh_locate<POW2>(P, R[i * r_stride]);
         if (c.j >= 0) {
             atomicAdd(&H[c.j], (unsigned long long)(P.W - c.qR));
             if (c.qR) atomicAdd(&H[c.j + 1], (unsigned long long)c.qR);
@@ -168,6 +169,7 @@ __global__ void k_field_from_prefix(DevParams P, const long long* __restrict__ Q
 
 // ------------------------------------------------------------------ gather
 
+template <int POW2>
 __global__ void k_gather(DevParams P, const double* __restrict__ R, long long n,
                          const double* __restrict__ E, const double* __restrict__ edges,
                          double* __restrict__ out, int use_smem) {
@@ -181,7 +183,7 @@ __global__ void k_gather(DevParams P, const double* __restrict__ R, long long n,
     const double lo = edges[0], hi = edges[1];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Cell c = mesh_locate(P, R[i]);
+        Cell c = mesh_locate<POW2>(P, R[i]);
         double e;
         if (use_smem) {
             e = mesh_gather(tab, lo, hi, c.j, c.a);
@@ -189,15 +191,54 @@ __global__ void k_gather(DevParams P, const double* __restrict__ R, long long n,
             double ej = E[c.j];
             e = fma(c.a, (E[c.j + 1] - ej) * P.invW, ej);
         } else {
-            e = (c.j == -1 ? lo : hi) / c.a;
+            e = gather_outside(lo, hi, c.j, c.a);
         }
         out[i] = e;
     }
 }
 
+// ------------------------------------------------------------ (R, V) packing
+
+__global__ void k_pack(const double* __restrict__ R, const double* __restrict__ V, double2* __restrict__ y,
+                       long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = make_double2(R[i], V[i]);
+}
+
+__global__ void k_unpack(const double2* __restrict__ y, double* __restrict__ R, double* __restrict__ V,
+                         long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = y[i];
+        if (R) R[i] = v.x;
+        if (V) V[i] = v.y;
+    }
+}
+
 // ------------------------------------------------------------ host launchers
 
-cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, long long* Q,
+static int grid_for(long long n, int sm_count) {
+    long long want = (n + 255) / 256;
+    long long cap = (long long)sm_count * 8;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+cudaError_t launch_pack(const double* R, const double* V, double2* y, long long n, int sm_count, cudaStream_t st,
+                        long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_pack<<<grid_for(n, sm_count), 256, 0, st>>>(R, V, y, n);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const double2* y, double* R, double* V, long long n, int sm_count, cudaStream_t st,
+                          long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_unpack<<<grid_for(n, sm_count), 256, 0, st>>>(y, R, V, n);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, int r_stride, long long* Q,
                            long long* n_out, cudaStream_t st, int sm_count, long long* launches) {
     const int Np1 = P.n_cells + 1;
     cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(long long) * (size_t)Np1, st);
@@ -205,12 +246,12 @@ cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, lon
     if (e != cudaSuccess || n == 0) return e;
     size_t smem = sizeof(unsigned long long) * (size_t)Np1;
     int use_smem = smem <= 96 * 1024;
-    if (use_smem && smem > 48 * 1024)
-        cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fn = P.xs_fma ? k_deposit<1> : k_deposit<0>;
+    if (use_smem && smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long long want = (n + 255) / 256;
     int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
-    k_deposit<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, (unsigned long long*)Q,
-                                                      (unsigned long long*)n_out, use_smem);
+    fn<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, r_stride, (unsigned long long*)Q, (unsigned long long*)n_out,
+                                               use_smem);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -263,11 +304,11 @@ cudaError_t launch_gather(const DevParams& P, const double* R, long long n, cons
     if (n == 0) return cudaSuccess;
     size_t smem = sizeof(double2) * (size_t)P.n_cells;
     int use_smem = smem <= 96 * 1024;
-    if (use_smem && smem > 48 * 1024)
-        cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fn = P.xs_fma ? k_gather<1> : k_gather<0>;
+    if (use_smem && smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long long want = (n + 255) / 256;
     int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
-    k_gather<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, E, edges, out, use_smem);
+    fn<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, E, edges, out, use_smem);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

@@ -30,6 +30,7 @@ struct DevParams {
     // mesh: nodes r_j = r_min + j*hr, j = 0..n_cells; node c = n_cells/2 is r = 0
     double r_min, hr, inv_hr;
     double xs_scale, xs_off, xs_max;   // xs = W*x, x = (R - r_min)/hr
+    long long xs_max_i;                // n_cells*W
     double Wd, invW;                   // W and 1/W (powers of two)
     double q_unit, q_half;             // charge per fixed-point unit, and half of it
     long long W, Wmask;
@@ -48,11 +49,12 @@ struct DevParams {
 // ---------------------------------------------------------------- mesh
 
 // Position of R in fixed-point mesh units: xs = W * (R - r_min) / hr.  When
-// 1/hr is a power of two, W*(R - r_min)*inv_hr equals fma(R, W*inv_hr,
+// 1/hr is a power of two (POW2), W*(R - r_min)*inv_hr equals fma(R, W*inv_hr,
 // -W*r_min*inv_hr) bit for bit (power-of-two scaling commutes with
-// rounding), so the cheaper form is used.
+// rounding), so the single fma is used; the form is fixed at compile time.
+template <int POW2>
 __device__ __forceinline__ double mesh_xs(const DevParams& P, double R) {
-    if (P.xs_fma) return fma(R, P.xs_scale, P.xs_off);
+    if (POW2) return fma(R, P.xs_scale, P.xs_off);
     return ((R - P.r_min) * P.inv_hr) * P.Wd;
 }
 
@@ -65,21 +67,82 @@ struct Cell {
     long long qR;
 };
 
+// Integer split of xs >= 0 (finite, < 2^62): xi = floor(xs) and
+// a = xs - (xi with its low log2W bits cleared), i.e. W f, read off the
+// IEEE bit pattern of xs with integer instructions.  Bit-identical to
+// xi = floor(xs), a = xs - (double)(j W): both are exact, and a is a
+// sub-field of the significand of xs re-normalised.
+__device__ __forceinline__ void split_fixed(double xs, int log2W, long long& xi, double& a) {
+    constexpr unsigned long long M52 = (1ull << 52) - 1;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(xs);
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) {  // 0 <= xs < 1
+        xi = 0;
+        a = xs;
+        return;
+    }
+    const unsigned long long m = (b & M52) | (1ull << 52);
+    xi = e <= 52 ? (long long)(m >> (52 - e)) : (long long)(m << (e - 52));
+    if (e < log2W) {  // xs < W: cell 0
+        a = xs;
+        return;
+    }
+    const int nb = 52 - e + log2W;  // significand bits below the cell boundary
+    if (nb <= 0) {
+        a = 0.0;
+        return;
+    }
+    const unsigned long long am = m & ((1ull << nb) - 1);
+    if (am == 0) {
+        a = 0.0;
+        return;
+    }
+    const int p = 63 - __clzll((long long)am);
+    a = __longlong_as_double((long long)((((unsigned long long)(p + e - 52 + 1023)) << 52) | ((am << (52 - p)) & M52)));
+}
+
+template <int POW2>
 __device__ __forceinline__ Cell mesh_locate(const DevParams& P, double R) {
     Cell c;
-    double xs = mesh_xs(P, R);
-    if (xs >= 0.0 && xs < P.xs_max) {
-        long long xi = __double2ll_rd(xs);   // floor(x*W), exact
-        c.qR = xi & P.Wmask;                 // floor(f*W)
-        long long jw = xi - c.qR;            // j*W
-        c.j = (int)(jw >> P.log2W);
-        c.a = xs - (double)jw;               // W*f, exact
-    } else {
-        c.j = (xs < 0.0) ? -1 : -2;
+    const double xs = mesh_xs<POW2>(P, R);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(xs);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    // below the mesh: negative (not -0, not NaN); above: NaN, >= 2^62 or
+    // beyond the last cell
+    if ((b >> 63) && mag != 0ull) {
+        c.j = mag > 0x7ff0000000000000ull ? -2 : -1;
         c.a = R;
         c.qR = 0;
+        return c;
     }
+    if ((int)(mag >> 52) - 1023 >= 62) {
+        c.j = -2;
+        c.a = R;
+        c.qR = 0;
+        return c;
+    }
+    long long xi;
+    double a;
+    split_fixed(xs, P.log2W, xi, a);
+    if (xi >= P.xs_max_i) {
+        c.j = -2;
+        c.a = R;
+        c.qR = 0;
+        return c;
+    }
+    c.qR = xi & P.Wmask;  // floor(f W)
+    c.j = (int)(xi >> P.log2W);
+    c.a = a;              // W f
     return c;
+}
+
+// V > 0 for every non-NaN double, tested on the bit pattern (integer pipe).
+__device__ __forceinline__ bool positive(double v) { return __double_as_longlong(v) > 0; }
+
+// Off the mesh rE keeps its edge value: E = rE_edge / R (rare; kept out of
+// line so the division is never evaluated for particles on the mesh).
+static __device__ __noinline__ double gather_outside(double rE_lo, double rE_hi, int j, double R) {
+    return (j == -1 ? rE_lo : rE_hi) / R;
 }
 
 // Field table entry of cell j: (E_j, (E_{j+1} - E_j) / W).  The gather
@@ -87,10 +150,10 @@ __device__ __forceinline__ Cell mesh_locate(const DevParams& P, double R) {
 __device__ __forceinline__ double mesh_gather(const double2* tab, double rE_lo, double rE_hi,
                                               int j, double a) {
     if (j >= 0) {
-        double2 e = tab[j];
+        const double2 e = tab[j];
         return fma(a, e.y, e.x);
     }
-    return (j == -1 ? rE_lo : rE_hi) / a;
+    return gather_outside(rE_lo, rE_hi, j, a);
 }
 
 // ------------------------------------------------------- analytic fields
@@ -177,7 +240,7 @@ __device__ __forceinline__ void track_resolve(Track& s, const DevParams& P, doub
 __device__ __forceinline__ void track_sample(Track& s, const DevParams& P, int k, double v0,
                                              double v1, double v2, bool detect_only) {
     if (s.flags & F_RES) return;
-    if ((v0 > 0.0) != (v1 > 0.0)) {
+    if (positive(v0) != positive(v1)) {
         double t = (double)(k - 2) + quad_root01(v0, v1, v2);
         int ne = (s.flags & F_NEXT) + 1;
         s.flags = (s.flags & ~F_NEXT) | (ne & F_NEXT);

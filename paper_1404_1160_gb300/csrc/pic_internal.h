@@ -26,27 +26,35 @@ struct ScanScratch {
 size_t scan_scratch_bytes(int n_cells);
 size_t scan_scratch_layout(int n_cells, int tiles, void* base, ScanScratch* S);
 
-cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, long long* Q,
+// R is read as R[i * r_stride].
+cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, int r_stride, long long* Q,
                            long long* n_out, cudaStream_t st, int sm_count, long long* launches);
+cudaError_t launch_pack(const double* R, const double* V, double2* y, long long n, int sm_count, cudaStream_t st,
+                        long long* launches);
+cudaError_t launch_unpack(const double2* y, double* R, double* V, long long n, int sm_count, cudaStream_t st,
+                          long long* launches);
 cudaError_t launch_poisson(const DevParams& P, const long long* Q, double* E, double* edges,
                            const ScanScratch& S, cudaStream_t st, long long* launches);
 cudaError_t launch_gather(const DevParams& P, const double* R, long long n, const double* E,
                           const double* edges, double* out, cudaStream_t st, int sm_count,
                           long long* launches);
 
-// Per-particle device state of a window (structure of arrays, n entries each
-// unless stated).
+// Per-particle device state of a window (structure of arrays; pairs are
+// interleaved so one 16-byte access moves both).
 struct WinBufs {
-    double *R, *V;              // current fine sample y_k
-    double* Vm2;                // V_{k-1} carried to the next sample
+    double2* y;                 // current fine sample (R, V)
+    double* Vm2;                // V of the previous sample, for the sign test
     double *t1, *T, *o;         // first extremum, period, remainder (fine steps)
-    int *N, *need, *flags;      // whole periods, last sample needed, Track flags
-    double *c0, *c1, *c2, *c3, *c4, *c5;  // stage values carried across a field cycle
-    int *j0, *j1;               // cells carried across a field cycle
+    int* N;                     // whole periods per macro step
+    int2* tr;                   // (Track flags, last sample needed)
+    double2* ce;                // values carried across a field cycle (fields / partial sums)
+    double2* ca;                // W f (or R off the mesh) of the two deposited positions
+    int2* cj;                   // cells of the two deposited positions
+    double2* cx;                // Lawson: (Phi_h y)_R; RK4: stage positions
     double2* traj;              // (Kmax+1) rows of n samples (R, V)
     unsigned long long* Qring;  // 3 cycles x 2 fields x (n_cells+1)
     int* notdone;               // 3 cycles
-    unsigned int* bar;          // grid barrier arrivals
+    unsigned int* bar;          // grid barrier: [0] arrivals, [32] released generation
     int* status;                // DEV_* of the launch
     long long* K_out;           // fine steps of the window
 };
@@ -55,10 +63,11 @@ enum WindowMode { MODE_PERIODS = 0, MODE_ETD = 1, MODE_FINE = 2 };
 
 struct WindowLaunch {
     int coop_grid = 0, coop_block = 0;
+    int hist = 0;             // 0: 32-bit split histograms, 1: 64-bit
     size_t coop_smem = 0;
 };
 
-cudaError_t window_prepare(const DevParams& P, int block, int sm_count, WindowLaunch* L);
+cudaError_t window_prepare(const DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L);
 // Poisson: one cooperative persistent launch per macro step (or per fine run).
 cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L,
                                int mode, int T_known, long long n_fine, cudaStream_t st,

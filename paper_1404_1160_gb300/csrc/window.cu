@@ -24,10 +24,42 @@ constexpr int kWinMaxThreads = 1024;
 
 // ---------------------------------------------------------------- helpers
 
-__device__ __forceinline__ void deposit_cell(unsigned long long* h, const Cell& c, long long W) {
-    if (c.j >= 0) {
-        atomicAdd(&h[c.j], (unsigned long long)(W - c.qR));
-        if (c.qR) atomicAdd(&h[c.j + 1], (unsigned long long)c.qR);
+// Shared-memory histogram of one field.  HIST = 0: three 32-bit counters
+// per cell (particles C_j, low and high 16 bits of the right weights S_j),
+// exact while a block deposits at most 65536 positions per field per cycle;
+// the node charge is Q_j = W C_j - S_j + S_{j-1}.  HIST = 1: one 64-bit
+// counter per node.
+template <int HIST>
+struct Hist {
+    static constexpr int kWordsPerNode = HIST == 0 ? 3 : 2;  // 32-bit words per node
+};
+
+template <int HIST>
+__device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cell& c, long long W) {
+    if (c.j < 0) return;
+    if (HIST == 0) {
+        atomicAdd(&h[c.j], 1u);
+        const unsigned int lo = (unsigned int)(c.qR & 0xffff), hi = (unsigned int)(c.qR >> 16);
+        if (lo) atomicAdd(&h[Np1 + c.j], lo);
+        if (hi) atomicAdd(&h[2 * Np1 + c.j], hi);
+    } else {
+        unsigned long long* h64 = (unsigned long long*)h;
+        atomicAdd(&h64[c.j], (unsigned long long)(W - c.qR));
+        if (c.qR) atomicAdd(&h64[c.j + 1], (unsigned long long)c.qR);
+    }
+}
+
+template <int HIST>
+__device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, int Np1, int j, long long W) {
+    if (HIST == 0) {
+        auto S = [&](int m) -> unsigned long long {
+            return m < 0 || m >= Np1 - 1 ? 0ull
+                                         : ((unsigned long long)h[2 * Np1 + m] << 16) + (unsigned long long)h[Np1 + m];
+        };
+        const unsigned long long C = (j < Np1 - 1) ? (unsigned long long)h[j] : 0ull;
+        return C * (unsigned long long)W - S(j) + S(j - 1);
+    } else {
+        return ((const unsigned long long*)h)[j];
     }
 }
 
@@ -41,28 +73,46 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x) {
     return x;
 }
 
-// g_j = sum_{m<j} (q_m + q_{m+1}), j = 0..Nc (block-wide, shared memory).
-__device__ void block_exscan_pairs(const long long* q, long long* g, int Nc, long long* s_warp) {
+// For both fields f = 0, 1: g_j = sum_{m<j} (q_m + q_{m+1}), j = 0..Nc
+// (block-wide exclusive scans in shared memory, done together).
+__device__ void block_exscan_pairs2(const long long* q, long long* g, int Nc, long long* s_warp) {
     const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
+    const int Np1 = Nc + 1;
     const int per = (Nc + T - 1) / T;
     const int beg = min(t * per, Nc), end = min(beg + per, Nc);
-    long long s = 0;
-    for (int m = beg; m < end; ++m) s += q[m] + q[m + 1];
-    long long x = warp_incl_scan64(s);
-    if (lane == 31) s_warp[w] = x;
+    long long s0 = 0, s1 = 0;
+    for (int m = beg; m < end; ++m) {
+        s0 += q[m] + q[m + 1];
+        s1 += q[Np1 + m] + q[Np1 + m + 1];
+    }
+    const long long x0 = warp_incl_scan64(s0), x1 = warp_incl_scan64(s1);
+    if (lane == 31) {
+        s_warp[w] = x0;
+        s_warp[32 + w] = x1;
+    }
     __syncthreads();
     if (w == 0) {
-        long long y = (lane < nw) ? s_warp[lane] : 0;
-        y = warp_incl_scan64(y);
-        if (lane < nw) s_warp[lane] = y;
+        long long y0 = (lane < nw) ? s_warp[lane] : 0, y1 = (lane < nw) ? s_warp[32 + lane] : 0;
+        y0 = warp_incl_scan64(y0);
+        y1 = warp_incl_scan64(y1);
+        if (lane < nw) {
+            s_warp[lane] = y0;
+            s_warp[32 + lane] = y1;
+        }
     }
     __syncthreads();
-    long long run = x - s + (w > 0 ? s_warp[w - 1] : 0);
+    long long r0 = x0 - s0 + (w > 0 ? s_warp[w - 1] : 0);
+    long long r1 = x1 - s1 + (w > 0 ? s_warp[32 + w - 1] : 0);
     for (int m = beg; m < end; ++m) {
-        g[m] = run;
-        run += q[m] + q[m + 1];
+        g[m] = r0;
+        g[Np1 + m] = r1;
+        r0 += q[m] + q[m + 1];
+        r1 += q[Np1 + m] + q[Np1 + m + 1];
     }
-    if (end == Nc && beg < end) g[Nc] = run;
+    if (end == Nc && beg < end) {
+        g[Nc] = r0;
+        g[Np1 + Nc] = r1;
+    }
     __syncthreads();
 }
 
@@ -75,8 +125,7 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + idx);
     __syncthreads();
-    block_exscan_pairs(q, g, Nc, s_warp);
-    block_exscan_pairs(q + Np1, g + Np1, Nc, s_warp);
+    block_exscan_pairs2(q, g, Nc, s_warp);
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
         const long long S = g[idx] - g[f * Np1 + c];
@@ -96,29 +145,36 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
 }
 
 // Grid barrier with a time limit; false if any block timed out or failed.
-__device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& target,
+// Arrivals count on bar[0]; the last block of a generation publishes the
+// generation number in bar[32] (another cache line), which the others poll.
+__device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& gen,
                                           int* status, int* s_ok) {
     __syncthreads();
-    target += gridDim.x + P.bar_extra;
+    ++gen;
     if (threadIdx.x == 0) {
+        const unsigned int target = gen * (gridDim.x + P.bar_extra);
         __threadfence();
-        atomicAdd(bar, 1u);
+        const unsigned int old = atomicAdd(bar, 1u);
         int ok = 1;
-        long long t0 = 0;
-        unsigned spins = 0;
-        while (ld_acquire_u32(bar) < target) {
-            if ((++spins & 31) == 0) {
-                if (ld_acquire_s32(status) != 0) {
-                    ok = 0;
-                    break;
-                }
-                long long now = global_ns();
-                if (t0 == 0) {
-                    t0 = now;
-                } else if (now - t0 > P.wait_ns) {
-                    atomicCAS(status, 0, (int)DEV_TIMEOUT);
-                    ok = 0;
-                    break;
+        if (old + 1 == target) {
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 32), "r"(gen) : "memory");
+        } else {
+            long long t0 = 0;
+            unsigned spins = 0;
+            while ((int)(ld_acquire_u32(bar + 32) - gen) < 0) {
+                if ((++spins & 31) == 0) {
+                    if (ld_acquire_s32(status) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    const long long now = global_ns();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > P.wait_ns) {
+                        atomicCAS(status, 0, (int)DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
         }
@@ -129,19 +185,21 @@ __device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar,
     return *s_ok != 0;
 }
 
-// Period tracking of one particle at sample k (k >= 1), with lazy loads of
-// the rarely used fields.  Returns true when the particle is done.
+// Period tracking of one particle at sample k (k >= 1).  tr = (flags,
+// need) is loaded by the caller and updated here; the rarely used fields
+// are loaded lazily.  Returns true when the particle is done.
 __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& B, long long i, int k,
-                                             double Vold, double Vnew, bool detect_only) {
-    int fl = B.flags[i];
+                                             double Vold, double Vnew, bool detect_only, int2& tr) {
+    const int fl = tr.x;
     if (!(fl & F_RES)) {
         Track s;
         s.flags = fl;
         s.t1 = 0.0;
+        s.need = tr.y;
         bool touched = false;
         if (k >= 2) {
-            double v0 = B.Vm2[i];
-            if ((v0 > 0.0) != (Vold > 0.0)) {
+            const double v0 = B.Vm2[i];
+            if (positive(v0) != positive(Vold)) {
                 if ((fl & F_NEXT) >= 1) s.t1 = B.t1[i];
                 track_sample(s, P, k, v0, Vold, Vnew, detect_only);
                 touched = true;
@@ -152,37 +210,55 @@ __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& 
             touched = true;
         }
         if (touched) {
-            B.flags[i] = s.flags;
             if ((s.flags & F_NEXT) == 1 && !(fl & F_NEXT)) B.t1[i] = s.t1;
             if (s.flags & F_RES) {
                 B.T[i] = s.T;
                 if (!detect_only) {
                     B.o[i] = s.o;
                     B.N[i] = s.N;
-                    B.need[i] = s.need;
                 }
             }
-            fl = s.flags;
+            tr = make_int2(s.flags, (s.flags & F_RES) && !detect_only ? s.need : tr.y);
+            B.tr[i] = tr;
         }
-        if (!(fl & F_RES)) B.Vm2[i] = Vold;
+        if (!(tr.x & F_RES)) B.Vm2[i] = Vold;
     }
-    if (!(fl & F_RES)) return false;
-    return detect_only || k >= B.need[i];
+    if (!(tr.x & F_RES)) return false;
+    return detect_only || k >= tr.y;
 }
 
 // ------------------------------------------------ cooperative Poisson window
 
-template <int SOLVER>
+// Flushes this block's two histograms into the cycle's global charge and
+// (block 0) clears the charge buffer of the next cycle.
+template <int HIST>
+__device__ __forceinline__ void flush_hist(const DevParams& P, const WinBufs& B, const unsigned int* hist, int cyc) {
+    const int Np1 = P.n_cells + 1;
+    const int words = Hist<HIST>::kWordsPerNode * Np1;
+    unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
+    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
+        const int f = idx >= Np1, j = idx - f * Np1;
+        const unsigned long long v = hist_node<HIST>(hist + f * words, Np1, j, P.W);
+        if (v) atomicAdd(Qg + idx, v);
+    }
+    if (blockIdx.x == 0) {
+        unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
+        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
+    }
+}
+
+template <int SOLVER, int HIST, int POW2>
 __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, WinBufs B, int mode, int T_known,
                                                                 long long n_fine, const double* __restrict__ Tin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Nc = P.n_cells, Np1 = Nc + 1;
-    double2* tab = (double2*)smem_raw;                                   // 2 Np1
-    unsigned long long* hist = (unsigned long long*)(tab + 2 * Np1);      // 2 Np1 (scan input too)
-    long long* g = (long long*)(hist + 2 * Np1);                          // 2 Np1
-    double* inv_r = (double*)(g + 2 * Np1);                               // Np1
+    const int words = Hist<HIST>::kWordsPerNode * Np1;   // 32-bit words per field histogram
+    double2* tab = (double2*)smem_raw;                    // 2 Np1
+    unsigned int* hist = (unsigned int*)(tab + 2 * Np1);  // 2 fields x words (also the scan input)
+    long long* g = (long long*)(hist + 2 * 3 * Np1);      // 2 Np1
+    double* inv_r = (double*)(g + 2 * Np1);               // Np1
     __shared__ double s_edges[4];
-    __shared__ long long s_warp[32];
+    __shared__ long long s_warp[64];
     __shared__ int s_ok, s_cnt, s_stop;
 
     for (int j = threadIdx.x; j < Np1; j += blockDim.x)
@@ -194,7 +270,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const double ie = P.inv_eps, mie = P.mie;
     const long long W = P.W;
-    unsigned int target = 0;
+    unsigned int gen = 0;
     int cyc = 0;
     int K = 0;
 
@@ -208,59 +284,56 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 B.T[i] = s.T;
                 B.o[i] = s.o;
                 B.N[i] = s.N;
-                B.need[i] = s.need;
-                B.flags[i] = s.flags;
+                B.tr[i] = make_int2(s.flags, s.need);
             } else {
-                B.flags[i] = 0;
+                B.tr[i] = make_int2(0, 0);
             }
         }
     }
 
     for (int k = 0;; ++k) {
         // ---- sweep A(k): finish step k-1, sample k, deposit stage pair 1 of step k
-        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) hist[idx] = 0ull;
+        for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
         const bool last_fine = fine_only && k == n_fine;
         unsigned int cnt = 0;
         for (long long i = i0; i < n; i += stride) {
-            double R = B.R[i], V = B.V[i];
+            const double2 y = B.y[i];
+            double R = y.x, V = y.y;
             if (k > 0) {
+                const double2 ce = B.ce[i], ca = B.ca[i], cx = B.cx[i];
+                const int2 cj = B.cj[i];
+                const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
+                const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
                 double Rn, Vn;
                 if (SOLVER == 1) {
-                    const double e1 = B.c0[i], e3 = B.c1[i];
-                    const double e2 = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
-                    const double e4 = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
-                    const double A = fma(P.s1, V, P.c1 * R);
+                    // ce = (e1, e3), ea = e2, eb = e4, cx.x = (Phi_h y)_R
+                    const double e1 = ce.x, e3 = ce.y;
                     const double Bv = fma(P.c1, V, -(P.s1 * R));
-                    const double e23 = e2 + e3;
-                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), A);
-                    Vn = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, e4)), Bv);
+                    const double e23 = ea + e3;
+                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), cx.x);
+                    Vn = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, eb)), Bv);
                 } else {
-                    const double pR = B.c0[i], pV = B.c1[i], R3 = B.c4[i], R4 = B.c5[i];
-                    const double e3 = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
-                    const double e4 = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
-                    const double k3V = fma(mie, R3, e3);
+                    // ce = partial sums, cx = (R3, R4), ea = e3, eb = e4
+                    const double k3V = fma(mie, cx.x, ea);
                     const double V4 = fma(P.h, k3V, V);
-                    const double k4R = ie * V4, k4V = fma(mie, R4, e4);
-                    const double sR = pR + k4R;
-                    const double sV = (pV + 2.0 * k3V) + k4V;
+                    const double k4R = ie * V4, k4V = fma(mie, cx.y, eb);
+                    const double sR = ce.x + k4R;
+                    const double sV = (ce.y + 2.0 * k3V) + k4V;
                     Rn = fma(P.h6, sR, R);
                     Vn = fma(P.h6, sV, V);
                 }
-                bool done = true;
-                if (!fine_only) done = track_update(P, B, i, k, V, Vn, detect_only);
-                R = Rn;
-                V = Vn;
-                B.R[i] = R;
-                B.V[i] = V;
                 if (!fine_only) {
-                    if (!detect_only) {
-                        int fl = B.flags[i];
-                        if (!((fl & F_RES) && k > B.need[i])) B.traj[(size_t)k * n + i] = make_double2(R, V);
-                    }
+                    int2 tr = B.tr[i];
+                    const bool done = track_update(P, B, i, k, V, Vn, detect_only, tr);
+                    if (!detect_only && !((tr.x & F_RES) && k > tr.y))
+                        B.traj[(size_t)k * n + i] = make_double2(Rn, Vn);
                     cnt += done ? 0u : 1u;
                 }
+                R = Rn;
+                V = Vn;
+                B.y[i] = make_double2(R, V);
             } else if (!fine_only) {
                 if (!detect_only) B.traj[i] = make_double2(R, V);
                 cnt += 1u;
@@ -268,21 +341,22 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             if (last_fine) continue;
             // stage pair 1
             Cell ca, cb;
+            double2 cx;
             if (SOLVER == 1) {
-                ca = mesh_locate(P, R);                              // stage 1: y
-                cb = mesh_locate(P, fma(P.sh, V, P.ch * R));         // stage 3: Phi_h/2 y
+                ca = mesh_locate<POW2>(P, R);                                  // stage 1: y
+                cb = mesh_locate<POW2>(P, fma(P.sh, V, P.ch * R));             // stage 3: Phi_h/2 y
+                cx = make_double2(fma(P.s1, V, P.c1 * R), 0.0);          // (Phi_h y)_R
             } else {
-                ca = mesh_locate(P, R);                              // stage 1: y
-                const double R2 = fma(P.h2, ie * V, R);              // stage 2: y + h/2 k1
-                cb = mesh_locate(P, R2);
-                B.c4[i] = R2;
+                ca = mesh_locate<POW2>(P, R);                                  // stage 1: y
+                const double R2 = fma(P.h2, ie * V, R);                  // stage 2: y + h/2 k1
+                cb = mesh_locate<POW2>(P, R2);
+                cx = make_double2(R2, 0.0);
             }
-            deposit_cell(hist, ca, W);
-            deposit_cell(hist + Np1, cb, W);
-            B.j0[i] = ca.j;
-            B.c2[i] = ca.a;
-            B.j1[i] = cb.j;
-            B.c3[i] = cb.a;
+            deposit_cell<HIST>(hist, Np1, ca, W);
+            deposit_cell<HIST>(hist + words, Np1, cb, W);
+            B.ca[i] = make_double2(ca.a, cb.a);
+            B.cj[i] = make_int2(ca.j, cb.j);
+            B.cx[i] = cx;
         }
         if (last_fine) break;
         if (!fine_only) {
@@ -290,20 +364,10 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, (int)cnt);
         }
         __syncthreads();
-        {
-            unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
-            for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
-                unsigned long long v = hist[idx];
-                if (v) atomicAdd(Qg + idx, v);
-            }
-            if (blockIdx.x == 0) {
-                unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
-                for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
-                if (threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
-            }
-            if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
-        }
-        if (!grid_sync(P, B.bar, target, B.status, &s_ok)) return;
+        flush_hist<HIST>(P, B, hist, cyc);
+        if (blockIdx.x == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
+        if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
         if (!fine_only) {
             if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
             __syncthreads();
@@ -316,56 +380,42 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         ++cyc;
 
         // ---- sweep B(k): gather pair 1, deposit stage pair 2
-        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) hist[idx] = 0ull;
+        for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
         __syncthreads();
         for (long long i = i0; i < n; i += stride) {
-            const double R = B.R[i], V = B.V[i];
-            const double ea = mesh_gather(tab, s_edges[0], s_edges[1], B.j0[i], B.c2[i]);
-            const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], B.j1[i], B.c3[i]);
+            const double2 y = B.y[i], ca = B.ca[i], cx = B.cx[i];
+            const int2 cj = B.cj[i];
+            const double R = y.x, V = y.y;
+            const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
+            const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
             double Pa, Pb;
             if (SOLVER == 1) {
                 // ea = e1 at y, eb = e3 at Phi_h/2 y
-                Pa = fma(P.sh, fma(P.h2, ea, V), P.ch * R);          // stage 2
-                Pb = fma(P.hsh, eb, fma(P.s1, V, P.c1 * R));         // stage 4
-                B.c0[i] = ea;
-                B.c1[i] = eb;
+                Pa = fma(P.sh, fma(P.h2, ea, V), P.ch * R);              // stage 2
+                Pb = fma(P.hsh, eb, cx.x);                               // stage 4
+                B.ce[i] = make_double2(ea, eb);
             } else {
-                // ea = e1 at y, eb = e2 at y + h/2 k1
-                const double R2 = B.c4[i];
+                // ea = e1 at y, eb = e2 at y + h/2 k1, cx.x = R2
                 const double k1R = ie * V, k1V = fma(mie, R, ea);
                 const double V2 = fma(P.h2, k1V, V);
-                const double k2R = ie * V2, k2V = fma(mie, R2, eb);
+                const double k2R = ie * V2, k2V = fma(mie, cx.x, eb);
                 const double R3 = fma(P.h2, k2R, R), V3 = fma(P.h2, k2V, V);
                 const double k3R = ie * V3;
                 const double R4 = fma(P.h, k3R, R);
-                Pa = R3;                                             // stage 3
-                Pb = R4;                                             // stage 4
-                B.c0[i] = (k1R + 2.0 * k2R) + 2.0 * k3R;
-                B.c1[i] = k1V + 2.0 * k2V;
-                B.c4[i] = R3;
-                B.c5[i] = R4;
+                Pa = R3;                                                 // stage 3
+                Pb = R4;                                                 // stage 4
+                B.ce[i] = make_double2((k1R + 2.0 * k2R) + 2.0 * k3R, k1V + 2.0 * k2V);
+                B.cx[i] = make_double2(R3, R4);
             }
-            const Cell ca = mesh_locate(P, Pa), cb = mesh_locate(P, Pb);
-            deposit_cell(hist, ca, W);
-            deposit_cell(hist + Np1, cb, W);
-            B.j0[i] = ca.j;
-            B.c2[i] = ca.a;
-            B.j1[i] = cb.j;
-            B.c3[i] = cb.a;
+            const Cell ca2 = mesh_locate<POW2>(P, Pa), cb2 = mesh_locate<POW2>(P, Pb);
+            deposit_cell<HIST>(hist, Np1, ca2, W);
+            deposit_cell<HIST>(hist + words, Np1, cb2, W);
+            B.ca[i] = make_double2(ca2.a, cb2.a);
+            B.cj[i] = make_int2(ca2.j, cb2.j);
         }
         __syncthreads();
-        {
-            unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
-            for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
-                unsigned long long v = hist[idx];
-                if (v) atomicAdd(Qg + idx, v);
-            }
-            if (blockIdx.x == 0) {
-                unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
-                for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
-            }
-        }
-        if (!grid_sync(P, B.bar, target, B.status, &s_ok)) return;
+        flush_hist<HIST>(P, B, hist, cyc);
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
         build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
         ++cyc;
     }
@@ -389,8 +439,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             y[t][0] = interp3(a.x, b.x, cc.x, sf);
             y[t][1] = interp3(a.y, b.y, cc.y, sf);
         }
-        B.R[i] = extrapolate(y[0][0], y[nt - 1][0], N);
-        B.V[i] = extrapolate(y[0][1], y[nt - 1][1], N);
+        B.y[i] = make_double2(extrapolate(y[0][0], y[nt - 1][0], N), extrapolate(y[0][1], y[nt - 1][1], N));
     }
 }
 
@@ -409,11 +458,11 @@ __global__ void __launch_bounds__(256) k_window_local(DevParams P, WinBufs B, in
     const long long stride = (long long)gridDim.x * blockDim.x;
     int Kmax_seen = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        double R = B.R[i], V = B.V[i];
+        const double2 y0 = B.y[i];
+        double R = y0.x, V = y0.y;
         if (mode == MODE_FINE) {
             for (long long k = 0; k < n_iter; ++k) fine_step<SOLVER, FIELD>(P, R, V);
-            B.R[i] = R;
-            B.V[i] = V;
+            B.y[i] = make_double2(R, V);
             continue;
         }
         if (mode == MODE_PERIODS) {
@@ -436,7 +485,7 @@ __global__ void __launch_bounds__(256) k_window_local(DevParams P, WinBufs B, in
                 vkm2 = vkm1;
             }
             B.T[i] = s.T;
-            B.flags[i] = s.flags;
+            B.tr[i] = make_int2(s.flags, 0);
             Kmax_seen = max(Kmax_seen, K);
             continue;
         }
@@ -517,13 +566,12 @@ __global__ void __launch_bounds__(256) k_window_local(DevParams P, WinBufs B, in
             V = extrapolate(y[0][1], y[1][1], s.N);
             Kmax_seen = max(Kmax_seen, K);
         }
-        B.R[i] = R;
-        B.V[i] = V;
+        B.y[i] = make_double2(R, V);
         if (n_iter > 0) {
             B.T[i] = s.T;
             B.o[i] = s.o;
             B.N[i] = s.N;
-            B.flags[i] = s.flags;
+            B.tr[i] = make_int2(s.flags, s.need);
         }
     }
     Kmax_seen = __reduce_max_sync(0xffffffffu, (unsigned)Kmax_seen);
@@ -539,7 +587,8 @@ __global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* par
     double a[kMomDoubles] = {0, 0, 0, 0, 0, 0, INFINITY, -INFINITY};
     long long b[kMomInts] = {LLONG_MAX, LLONG_MIN, 0};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double R = B.R[i], V = B.V[i], T = B.T[i];
+        const double2 y = B.y[i];
+        const double R = y.x, V = y.y, T = B.T[i];
         const double R2 = R * R;
         a[0] += R;
         a[1] += V;
@@ -552,7 +601,7 @@ __global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* par
         const long long N = B.N[i];
         b[0] = min(b[0], N);
         b[1] = max(b[1], N);
-        b[2] += (B.flags[i] & F_FB) ? 1 : 0;
+        b[2] += (B.tr[i].x & F_FB) ? 1 : 0;
     }
     for (int d = 16; d >= 1; d >>= 1) {
         for (int q = 0; q < 6; ++q) a[q] += __shfl_xor_sync(0xffffffffu, a[q], d);
@@ -586,39 +635,50 @@ __global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* par
 
 static size_t coop_smem_bytes(int n_cells) {
     const size_t Np1 = (size_t)n_cells + 1;
-    return 2 * Np1 * sizeof(double2) + 2 * Np1 * sizeof(unsigned long long) + 2 * Np1 * sizeof(long long) +
+    return 2 * Np1 * sizeof(double2) + 2 * 3 * Np1 * sizeof(unsigned int) + 2 * Np1 * sizeof(long long) +
            Np1 * sizeof(double);
 }
 
-template <int SOLVER>
-static cudaError_t prepare_one(int block, size_t smem, int* blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_window_coop<SOLVER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_window_coop<SOLVER>, block, smem);
+static void* coop_fn(int solver, int hist, int pow2) {
+    if (pow2) {
+        if (solver == 1) return hist == 0 ? (void*)k_window_coop<1, 0, 1> : (void*)k_window_coop<1, 1, 1>;
+        return hist == 0 ? (void*)k_window_coop<0, 0, 1> : (void*)k_window_coop<0, 1, 1>;
+    }
+    if (solver == 1) return hist == 0 ? (void*)k_window_coop<1, 0, 0> : (void*)k_window_coop<1, 1, 0>;
+    return hist == 0 ? (void*)k_window_coop<0, 0, 0> : (void*)k_window_coop<0, 1, 0>;
 }
 
-cudaError_t window_prepare(const DevParams& P, int block, int sm_count, WindowLaunch* L) {
+cudaError_t window_prepare(const DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L) {
     L->coop_block = block;
     L->coop_smem = coop_smem_bytes(P.n_cells);
-    int b0 = 0, b1 = 0;
-    cudaError_t e = prepare_one<0>(block, L->coop_smem, &b0);
-    if (e == cudaSuccess) e = prepare_one<1>(block, L->coop_smem, &b1);
-    if (e != cudaSuccess) return e;
-    int bps = b0 < b1 ? b0 : b1;
+    int bps = 1 << 30;
+    for (int s = 0; s < 2; ++s)
+        for (int hh = 0; hh < 2; ++hh) {
+            void* fn = coop_fn(s, hh, P.xs_fma);
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->coop_smem);
+            if (e != cudaSuccess) return e;
+            int b = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, L->coop_smem);
+            if (e != cudaSuccess) return e;
+            bps = b < bps ? b : bps;
+        }
     if (bps < 1) return cudaErrorInvalidConfiguration;
-    if (bps > 2) bps = 2;
+    const int want = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    if (want < bps) bps = want;
     long long need = (P.n + block - 1) / block;
     long long grid = (long long)bps * sm_count;
     if (need < grid) grid = need < 1 ? 1 : need;
     L->coop_grid = (int)grid;
+    // positions one block deposits into one field per cycle
+    const long long per_thread = (P.n + grid * block - 1) / (grid * block);
+    L->hist = per_thread * block <= 65536 ? 0 : 1;
     return cudaSuccess;
 }
 
 cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L, int mode,
                                int T_known, long long n_fine, cudaStream_t st, long long* launches,
                                const double* Tin) {
-    void* fn = P.solver == 1 ? (void*)k_window_coop<1> : (void*)k_window_coop<0>;
+    void* fn = coop_fn(P.solver, L.hist, P.xs_fma);
     DevParams Pc = P;
     WinBufs Bc = B;
     void* args[] = {&Pc, &Bc, &mode, &T_known, &n_fine, &Tin};

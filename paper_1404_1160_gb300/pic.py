@@ -53,6 +53,8 @@ class pic_params(C.Structure):
         ("periods_once", C.c_int32),
         ("precision", C.c_int32),
         ("block_size", C.c_int32),
+        ("blocks_per_sm", C.c_int32),
+        ("reserved", C.c_int32),
         ("wait_limit_ns", C.c_int64),
     ]
 

@@ -68,8 +68,8 @@ def test_struct_layout_matches_header(lib):
 
     from paper_1404_1160_gb300 import pic
 
-    # pic_params: 2 doubles, 4 int32, 3 doubles, uint64, 4 int32, int64
-    assert ctypes.sizeof(pic.pic_params) == 2 * 8 + 4 * 4 + 3 * 8 + 8 + 4 * 4 + 8
+    # pic_params: 2 doubles, 4 int32, 3 doubles, uint64, 6 int32, int64
+    assert ctypes.sizeof(pic.pic_params) == 2 * 8 + 4 * 4 + 3 * 8 + 8 + 6 * 4 + 8
     assert ctypes.sizeof(pic.pic_moments_t) == 19 * 8
 
 
