@@ -79,13 +79,16 @@ typedef struct {
     int32_t  precision;        /* 0 = FP64 (only value served)                    */
     int32_t  block_size;       /* CUDA threads per block, 0 = library default     */
     int32_t  blocks_per_sm;    /* Poisson window blocks per SM, 0 = default (2)   */
-    int32_t  reserved;         /* must be 0                                       */
+    int32_t  sort_every;       /* macro steps between phase-space sorts of the
+                                  particle storage (0 = never, default 1); the
+                                  public particle order never changes          */
     int64_t  wait_limit_ns;    /* limit of every device-side wait, 0 = 2 s        */
 } pic_params;
 
 /* Fills p with the defaults of the paper-shaped Vlasov-Poisson run:
    eps 0.01, dt 0.1, Poisson, Lawson RK4, 100 steps per turn, 256 cells on
-   [-4, 4], total charge 1, W = 2^32, window cap 300, periods every step. */
+   [-4, 4], total charge 1, W = 2^32, window cap 300, periods every step,
+   phase-space sort every macro step. */
 void pic_default_params(pic_params* p);
 
 /* ---- handle-based run (the hot path) ----------------------------------- */

@@ -43,6 +43,7 @@ int check_params(const pic_params* p, bool need_mesh) {
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || (p->block_size & 31)))
         return PIC_ERR_INVALID_ARG;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_ERR_INVALID_ARG;
+    if (p->sort_every < 0) return PIC_ERR_INVALID_ARG;
     if (p->wait_limit_ns < 0) return PIC_ERR_INVALID_ARG;
     if (need_mesh || p->field_model == PIC_FIELD_POISSON) {
         if (p->n_cells < 2 || p->n_cells > 65536 || (p->n_cells & 1)) return PIC_ERR_INVALID_ARG;
@@ -118,16 +119,6 @@ int current_sm_count(int* sms) {
 cudaMemcpyKind kind_to(int ptr_kind) { return ptr_kind == PIC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_from(int ptr_kind) { return ptr_kind == PIC_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
-// Converts the per-particle step results to the public units.
-__global__ void k_export_periods(long long n, double h, const double* Ts, const int* N, const double* os,
-                                 double* T_out, long long* N_out, double* o_out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        if (T_out) T_out[i] = Ts[i] * h;
-        if (N_out) N_out[i] = (long long)N[i];
-        if (o_out) o_out[i] = os[i] * h;
-    }
-}
-
 }  // namespace
 
 struct pic_handle {
@@ -140,6 +131,13 @@ struct pic_handle {
     pic::WindowLaunch L;
     double* Tin = nullptr;   // periods of y^0 (fine steps) when periods_once
     double *tmpR = nullptr, *tmpV = nullptr;  // unpacked R, V for copies in and out
+    // storage order: slot s holds original particle perm[s] (phase-space sort)
+    int *perm = nullptr, *perm_alt = nullptr;
+    double2* y_alt = nullptr;
+    double* Tin_alt = nullptr;
+    int* skey = nullptr;
+    unsigned int* scount = nullptr;
+    pic::SortBufs sort;
     std::vector<void*> allocs;
     // field of the current positions
     long long *Qf = nullptr, *nout_f = nullptr;
@@ -195,6 +193,12 @@ cudaError_t reset_coop(pic_handle* h) {
     return e;
 }
 
+// Phase-space sort of the storage order before a window (see sort.cu).
+cudaError_t maybe_sort(pic_handle* h, long long step_index) {
+    if (h->prm.sort_every <= 0 || step_index % h->prm.sort_every != 0) return cudaSuccess;
+    return pic::launch_phase_sort(h->sort, h->n, h->sm_count, h->st, &h->launches);
+}
+
 int run_window(pic_handle* h, int mode, long long n_iter) {
     if (h->n == 0) return PIC_OK;
     cudaError_t e = cudaMemsetAsync(h->B.status, 0, sizeof(int), h->st);
@@ -203,13 +207,15 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         const long long reps = mode == pic::MODE_ETD ? n_iter : 1;
         for (long long s = 0; s < reps && e == cudaSuccess; ++s) {
-            e = reset_coop(h);
+            if (mode == pic::MODE_ETD) e = maybe_sort(h, h->n_steps + s);
+            if (e == cudaSuccess) e = reset_coop(h);
             if (e == cudaSuccess)
                 e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, mode == pic::MODE_FINE ? n_iter : 0,
                                             h->st, &h->launches, h->Tin);
         }
     } else {
-        e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
+        if (mode == pic::MODE_ETD) e = maybe_sort(h, 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
         if (e == cudaSuccess)
             e = pic::launch_window_local(h->dp, h->B, mode, T_known, mode == pic::MODE_PERIODS ? 0 : n_iter,
                                          h->block, h->sm_count, h->st, &h->launches, h->Tin);
@@ -239,6 +245,8 @@ void pic_default_params(pic_params* p) {
     p->periods_once = 0;
     p->precision = 0;
     p->block_size = 0;
+    p->blocks_per_sm = 0;
+    p->sort_every = 1;
     p->wait_limit_ns = 0;
 }
 
@@ -263,6 +271,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     if (rc) return rc;
     if (n < 0 || (n > 0 && (!r0 || !v0)) || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE))
         return PIC_ERR_INVALID_ARG;
+    if (n > 2147483647ll) return PIC_ERR_UNSUPPORTED;
     if (p->field_model == PIC_FIELD_POISSON) {
         if (p->n_cells > pic::kMaxCellsWindow) return PIC_ERR_UNSUPPORTED;
         if ((double)n * (double)p->weight_fixed >= 4.611686018427388e18) return PIC_ERR_OVERFLOW;
@@ -297,6 +306,14 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     ALLOC(B.tr, N);
     ALLOC(h->tmpR, N);
     ALLOC(h->tmpV, N);
+    ALLOC(h->perm, N);
+    if (p->sort_every > 0) {
+        ALLOC(h->perm_alt, N);
+        ALLOC(h->y_alt, N);
+        ALLOC(h->skey, N);
+        ALLOC(h->scount, pic::kSortBinsTotal);
+        if (p->periods_once) ALLOC(h->Tin_alt, N);
+    }
     if (p->field_model == PIC_FIELD_POISSON) {
         ALLOC(B.ce, N);
         ALLOC(B.ca, N);
@@ -339,11 +356,23 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
         e = cudaMemcpyAsync(h->tmpR, r0, sizeof(double) * N, kind_to(ptr_kind), h->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v0, sizeof(double) * N, kind_to(ptr_kind), h->st);
         if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, B.y, n, sms, h->st, &h->launches);
+        if (e == cudaSuccess) e = pic::launch_iota(h->perm, n, sms, h->st, &h->launches);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.T, 0, sizeof(double) * N, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.o, 0, sizeof(double) * N, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.N, 0, sizeof(int) * N, h->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(B.tr, 0, sizeof(int2) * N, h->st);
         rc = map_cuda(e);
+    }
+    if (!rc) {
+        pic::SortBufs& S = h->sort;
+        S.y = &h->B.y;
+        S.y_alt = &h->y_alt;
+        S.perm = &h->perm;
+        S.perm_alt = &h->perm_alt;
+        S.Tin = p->periods_once ? &h->Tin : nullptr;
+        S.Tin_alt = p->periods_once ? &h->Tin_alt : nullptr;
+        S.key = h->skey;
+        S.count = h->scount;
     }
     if (!rc && p->field_model == PIC_FIELD_POISSON)
         rc = map_cuda(pic::window_prepare(h->dp, h->block, p->blocks_per_sm, sms, &h->L));
@@ -469,9 +498,9 @@ int pic_get_particles(pic_handle* h, double* r, double* v, int ptr_kind) {
     const size_t bytes = sizeof(double) * (size_t)h->n;
     cudaError_t e;
     if (ptr_kind == PIC_PTR_DEVICE) {
-        e = pic::launch_unpack(h->B.y, r, v, h->n, h->sm_count, h->st, &h->launches);
+        e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, r, v, h->sm_count, h->st, &h->launches);
     } else {
-        e = pic::launch_unpack(h->B.y, h->tmpR, h->tmpV, h->n, h->sm_count, h->st, &h->launches);
+        e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, h->tmpR, h->tmpV, h->sm_count, h->st, &h->launches);
         if (e == cudaSuccess && r) e = cudaMemcpyAsync(r, h->tmpR, bytes, cudaMemcpyDeviceToHost, h->st);
         if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, h->tmpV, bytes, cudaMemcpyDeviceToHost, h->st);
     }
@@ -486,7 +515,7 @@ int pic_set_particles(pic_handle* h, const double* r, const double* v, int ptr_k
     const size_t bytes = sizeof(double) * (size_t)h->n;
     cudaError_t e = cudaMemcpyAsync(h->tmpR, r, bytes, kind_to(ptr_kind), h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v, bytes, kind_to(ptr_kind), h->st);
-    if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, h->B.y, h->n, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess) e = pic::launch_pack_perm(h->tmpR, h->tmpV, h->perm, h->n, h->B.y, h->sm_count, h->st, &h->launches);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
 }
@@ -502,15 +531,14 @@ int pic_get_periods(pic_handle* h, double* T, int64_t* N, double* o, int ptr_kin
     if (ptr_kind == PIC_PTR_HOST) {
         e = cudaMallocAsync(&tmp, n * (2 * sizeof(double) + sizeof(long long)), h->st);
         if (e != cudaSuccess) return map_cuda(e);
-        dT = T ? (double*)tmp : nullptr;
-        dO = o ? (double*)tmp + n : nullptr;
-        dN = N ? (long long*)((double*)tmp + 2 * n) : nullptr;
+        dT = (double*)tmp;
+        dO = (double*)tmp + n;
+        dN = (long long*)((double*)tmp + 2 * n);
     }
-    long long want = ((long long)n + 255) / 256;
-    int grid = (int)(want < (long long)h->sm_count * 4 ? want : (long long)h->sm_count * 4);
-    k_export_periods<<<grid, 256, 0, h->st>>>(h->n, h->dp.h, h->B.T, h->B.N, h->B.o, dT, dN, dO);
-    ++h->launches;
-    e = cudaGetLastError();
+    // per-slot results to the public order, in units of time
+    if (T) e = pic::launch_permute_d(h->B.T, h->perm, h->n, h->dp.h, 1, dT, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess && o) e = pic::launch_permute_d(h->B.o, h->perm, h->n, h->dp.h, 1, dO, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess && N) e = pic::launch_scatter_i(h->B.N, h->perm, h->n, dN, h->sm_count, h->st, &h->launches);
     if (ptr_kind == PIC_PTR_HOST) {
         if (e == cudaSuccess && T) e = cudaMemcpyAsync(T, dT, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
         if (e == cudaSuccess && o) e = cudaMemcpyAsync(o, dO, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -529,11 +557,12 @@ int pic_get_state(pic_handle* h, pic_state_t* out) {
     if (h->n == 0) return PIC_OK;
     if (!out->r || !out->v || !out->T) return PIC_ERR_INVALID_ARG;
     const size_t n = (size_t)h->n;
-    cudaError_t e = pic::launch_unpack(h->B.y, h->tmpR, h->tmpV, h->n, h->sm_count, h->st, &h->launches);
+    cudaError_t e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, h->tmpR, h->tmpV, h->sm_count, h->st, &h->launches);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->r, h->tmpR, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->v, h->tmpV, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     const double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out->T, Ts, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = pic::launch_permute_d(Ts, h->perm, h->n, 1.0, 1, h->tmpR, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->T, h->tmpR, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
 }
@@ -547,9 +576,10 @@ int pic_set_state(pic_handle* h, const pic_state_t* in) {
     if (n > 0) {
         e = cudaMemcpyAsync(h->tmpR, in->r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, in->v, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
-        if (e == cudaSuccess) e = pic::launch_pack(h->tmpR, h->tmpV, h->B.y, h->n, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess) e = pic::launch_pack_perm(h->tmpR, h->tmpV, h->perm, h->n, h->B.y, h->sm_count, h->st, &h->launches);
         double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(Ts, in->T, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpR, in->T, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = pic::launch_permute_d(h->tmpR, h->perm, h->n, 1.0, 0, Ts, h->sm_count, h->st, &h->launches);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     }
     if (e != cudaSuccess) return map_cuda(e);

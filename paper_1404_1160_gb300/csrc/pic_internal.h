@@ -78,6 +78,31 @@ cudaError_t launch_window_local(const DevParams& P, const WinBufs& B, int mode, 
                                 long long n_iter, int block, int sm_count, cudaStream_t st,
                                 long long* launches, const double* Tin);
 
+// Phase-space sort (sort.cu).  The pointers are swapped with their *_alt
+// buffers after each sort, so they are held by address.
+struct SortBufs {
+    double2** y;
+    double2** y_alt;
+    int** perm;              // slot -> original particle index
+    int** perm_alt;
+    double** Tin;            // periods kept from pic_init (may be NULL)
+    double** Tin_alt;
+    int* key;                // n
+    unsigned int* count;     // bins
+};
+size_t sort_scratch_bytes(long long n);
+cudaError_t launch_phase_sort(SortBufs& S, long long n, int sm_count, cudaStream_t st, long long* launches);
+cudaError_t launch_unpack_perm(const double2* y, const int* perm, long long n, double* R, double* V, int sm_count,
+                               cudaStream_t st, long long* launches);
+cudaError_t launch_pack_perm(const double* R, const double* V, const int* perm, long long n, double2* y, int sm_count,
+                             cudaStream_t st, long long* launches);
+cudaError_t launch_permute_d(const double* src, const int* perm, long long n, double scale, int scatter, double* dst,
+                             int sm_count, cudaStream_t st, long long* launches);
+cudaError_t launch_scatter_i(const int* src, const int* perm, long long n, long long* dst, int sm_count,
+                             cudaStream_t st, long long* launches);
+cudaError_t launch_iota(int* perm, long long n, int sm_count, cudaStream_t st, long long* launches);
+constexpr int kSortBinsTotal = 1024 * 32;
+
 // Reductions for pic_moments: per-block partial sums, combined on the host
 // in a fixed order.
 constexpr int kMomDoubles = 8;   // sumR sumV sumR2 sumV2 sumR4 sumT minT maxT

@@ -36,13 +36,20 @@ struct Hist {
 
 template <int HIST>
 __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cell& c, long long W) {
-    if (c.j < 0) return;
     if (HIST == 0) {
-        atomicAdd(&h[c.j], 1u);
+        // lanes of a warp that share a cell add their counts and weight
+        // halves first (one set of shared atomics per distinct cell)
+        const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)c.j);
         const unsigned int lo = (unsigned int)(c.qR & 0xffff), hi = (unsigned int)(c.qR >> 16);
-        if (lo) atomicAdd(&h[Np1 + c.j], lo);
-        if (hi) atomicAdd(&h[2 * Np1 + c.j], hi);
+        const unsigned int slo = __reduce_add_sync(peers, lo);
+        const unsigned int shi = __reduce_add_sync(peers, hi);
+        if (c.j >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicAdd(&h[c.j], (unsigned int)__popc(peers));
+            if (slo) atomicAdd(&h[Np1 + c.j], slo);
+            if (shi) atomicAdd(&h[2 * Np1 + c.j], shi);
+        }
     } else {
+        if (c.j < 0) return;
         unsigned long long* h64 = (unsigned long long*)h;
         atomicAdd(&h64[c.j], (unsigned long long)(W - c.qR));
         if (c.qR) atomicAdd(&h64[c.j + 1], (unsigned long long)c.qR);
@@ -268,6 +275,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     const long long n = P.n;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const double ie = P.inv_eps, mie = P.mie;
     const long long W = P.W;
     unsigned int gen = 0;
@@ -298,10 +306,18 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         __syncthreads();
         const bool last_fine = fine_only && k == n_fine;
         unsigned int cnt = 0;
-        for (long long i = i0; i < n; i += stride) {
-            const double2 y = B.y[i];
-            double R = y.x, V = y.y;
-            if (k > 0) {
+        // warp-uniform trip count: lanes past the end run with an empty cell
+        for (long long ib = i0 - lane; ib < n; ib += stride) {
+            const long long i = ib + lane;
+            const bool valid = i < n;
+            double R = 0.0, V = 0.0;
+            if (valid) {
+                const double2 y = B.y[i];
+                R = y.x;
+                V = y.y;
+            }
+            if (!valid) {
+            } else if (k > 0) {
                 const double2 ce = B.ce[i], ca = B.ca[i], cx = B.cx[i];
                 const int2 cj = B.cj[i];
                 const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
@@ -343,20 +359,23 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             Cell ca, cb;
             double2 cx;
             if (SOLVER == 1) {
-                ca = mesh_locate<POW2>(P, R);                                  // stage 1: y
-                cb = mesh_locate<POW2>(P, fma(P.sh, V, P.ch * R));             // stage 3: Phi_h/2 y
+                ca = mesh_locate<POW2>(P, R);                            // stage 1: y
+                cb = mesh_locate<POW2>(P, fma(P.sh, V, P.ch * R));       // stage 3: Phi_h/2 y
                 cx = make_double2(fma(P.s1, V, P.c1 * R), 0.0);          // (Phi_h y)_R
             } else {
-                ca = mesh_locate<POW2>(P, R);                                  // stage 1: y
+                ca = mesh_locate<POW2>(P, R);                            // stage 1: y
                 const double R2 = fma(P.h2, ie * V, R);                  // stage 2: y + h/2 k1
                 cb = mesh_locate<POW2>(P, R2);
                 cx = make_double2(R2, 0.0);
             }
+            if (!valid) ca.j = cb.j = -3;
             deposit_cell<HIST>(hist, Np1, ca, W);
             deposit_cell<HIST>(hist + words, Np1, cb, W);
-            B.ca[i] = make_double2(ca.a, cb.a);
-            B.cj[i] = make_int2(ca.j, cb.j);
-            B.cx[i] = cx;
+            if (valid) {
+                B.ca[i] = make_double2(ca.a, cb.a);
+                B.cj[i] = make_int2(ca.j, cb.j);
+                B.cx[i] = cx;
+            }
         }
         if (last_fine) break;
         if (!fine_only) {
@@ -382,9 +401,17 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         // ---- sweep B(k): gather pair 1, deposit stage pair 2
         for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
         __syncthreads();
-        for (long long i = i0; i < n; i += stride) {
-            const double2 y = B.y[i], ca = B.ca[i], cx = B.cx[i];
-            const int2 cj = B.cj[i];
+        for (long long ib = i0 - lane; ib < n; ib += stride) {
+            const long long i = ib + lane;
+            const bool valid = i < n;
+            double2 y = make_double2(0.0, 0.0), ca = make_double2(0.0, 0.0), cx = make_double2(0.0, 0.0);
+            int2 cj = make_int2(-3, -3);
+            if (valid) {
+                y = B.y[i];
+                ca = B.ca[i];
+                cx = B.cx[i];
+                cj = B.cj[i];
+            }
             const double R = y.x, V = y.y;
             const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
             const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
@@ -393,7 +420,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 // ea = e1 at y, eb = e3 at Phi_h/2 y
                 Pa = fma(P.sh, fma(P.h2, ea, V), P.ch * R);              // stage 2
                 Pb = fma(P.hsh, eb, cx.x);                               // stage 4
-                B.ce[i] = make_double2(ea, eb);
+                if (valid) B.ce[i] = make_double2(ea, eb);
             } else {
                 // ea = e1 at y, eb = e2 at y + h/2 k1, cx.x = R2
                 const double k1R = ie * V, k1V = fma(mie, R, ea);
@@ -404,14 +431,19 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 const double R4 = fma(P.h, k3R, R);
                 Pa = R3;                                                 // stage 3
                 Pb = R4;                                                 // stage 4
-                B.ce[i] = make_double2((k1R + 2.0 * k2R) + 2.0 * k3R, k1V + 2.0 * k2V);
-                B.cx[i] = make_double2(R3, R4);
+                if (valid) {
+                    B.ce[i] = make_double2((k1R + 2.0 * k2R) + 2.0 * k3R, k1V + 2.0 * k2V);
+                    B.cx[i] = make_double2(R3, R4);
+                }
             }
-            const Cell ca2 = mesh_locate<POW2>(P, Pa), cb2 = mesh_locate<POW2>(P, Pb);
+            Cell ca2 = mesh_locate<POW2>(P, Pa), cb2 = mesh_locate<POW2>(P, Pb);
+            if (!valid) ca2.j = cb2.j = -3;
             deposit_cell<HIST>(hist, Np1, ca2, W);
             deposit_cell<HIST>(hist + words, Np1, cb2, W);
-            B.ca[i] = make_double2(ca2.a, cb2.a);
-            B.cj[i] = make_int2(ca2.j, cb2.j);
+            if (valid) {
+                B.ca[i] = make_double2(ca2.a, cb2.a);
+                B.cj[i] = make_int2(ca2.j, cb2.j);
+            }
         }
         __syncthreads();
         flush_hist<HIST>(P, B, hist, cyc);

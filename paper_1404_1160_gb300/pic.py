@@ -54,7 +54,7 @@ class pic_params(C.Structure):
         ("precision", C.c_int32),
         ("block_size", C.c_int32),
         ("blocks_per_sm", C.c_int32),
-        ("reserved", C.c_int32),
+        ("sort_every", C.c_int32),
         ("wait_limit_ns", C.c_int64),
     ]
 

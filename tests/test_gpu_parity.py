@@ -232,6 +232,27 @@ def test_paper_workload_eps_1e_3():
     pic.pic_destroy(h)
 
 
+@pytest.mark.parametrize("field,solver", [(pic.PIC_FIELD_POISSON, pic.PIC_FINE_LAWSON_RK4), (pic.PIC_FIELD_POISSON, pic.PIC_FINE_RK4),
+                                          (pic.PIC_FIELD_DUFFING, pic.PIC_FINE_LAWSON_RK4)])
+def test_phase_space_sort_changes_no_result(field, solver):
+    # the storage order is an implementation detail: sorting every step,
+    # every third step or never must give the same bits in the public order
+    R0, V0 = inputs.gaussian_beam(9000, seed=21, r_cut=4.0)
+    out = []
+    for every in (0, 1, 3):
+        p = pic.pic_default_params(field_model=field, fine_solver=solver, sort_every=every, dt=0.1)
+        h = pic.pic_init(p, R0, V0)
+        pic.pic_step(h, 4)
+        R, V = pic.pic_get_particles(h)
+        T, N, o = pic.pic_get_periods(h)
+        st = pic.pic_get_state(h)
+        out.append((R, V, T, N, o, st["T"]))
+        pic.pic_destroy(h)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert bit_equal(a, b)
+
+
 # -------------------------------------------------------- state and failures
 
 
