@@ -77,8 +77,9 @@ typedef struct {
     int32_t  periods_once;     /* 1: periods computed once at pic_init and kept
                                   (the Duffing case of Sec. 4.1); 0: every step  */
     int32_t  precision;        /* 0 = FP64 (only value served)                    */
-    int32_t  block_size;       /* CUDA threads per block, 0 = library default     */
-    int32_t  blocks_per_sm;    /* Poisson window blocks per SM, 0 = default (2)   */
+    int32_t  block_size;       /* CUDA threads per block, 0 = library default
+                                  (1024 Poisson, 128 otherwise)                 */
+    int32_t  blocks_per_sm;    /* Poisson window blocks per SM, 0 = default (1)   */
     int32_t  sort_every;       /* macro steps between phase-space sorts of the
                                   particle storage (0 = never, default 1); the
                                   public particle order never changes          */

@@ -186,7 +186,7 @@ int read_status(pic_handle* h) {
 // Resets the per-launch synchronisation words of the cooperative window.
 cudaError_t reset_coop(pic_handle* h) {
     const size_t Np1 = (size_t)h->dp.n_cells + 1;
-    cudaError_t e = cudaMemsetAsync(h->B.Qring, 0, sizeof(unsigned long long) * 3 * 2 * Np1, h->st);
+    cudaError_t e = cudaMemsetAsync(h->B.Qring, 0, sizeof(unsigned long long) * 3 * 2 * Np1 * pic::kQPad, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.notdone, 0, sizeof(int) * 3, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.bar, 0, sizeof(unsigned int) * 64, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
@@ -286,7 +286,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     h->st = (cudaStream_t)stream;
     h->sm_count = sms;
     make_devparams(p, n, &h->dp);
-    h->block = p->block_size ? p->block_size : (p->field_model == PIC_FIELD_POISSON ? 512 : 128);
+    h->block = p->block_size ? p->block_size : (p->field_model == PIC_FIELD_POISSON ? 1024 : 128);
 
     const size_t N = (size_t)n;
     const size_t Np1 = (size_t)p->n_cells + 1;
@@ -295,10 +295,11 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     std::memset(&B, 0, sizeof(B));
     cudaError_t e = cudaSuccess;
     rc = PIC_OK;
-#define ALLOC(ptr, cnt) \
-    if (!rc) rc = dalloc(h, &(ptr), (cnt))
+#define ALLOC(ptr, cnt)                         \
+    do {                                        \
+        if (!rc) rc = dalloc(h, &(ptr), (cnt)); \
+    } while (0)
     ALLOC(B.y, N);
-    ALLOC(B.Vm2, N);
     ALLOC(B.t1, N);
     ALLOC(B.T, N);
     ALLOC(B.o, N);
@@ -317,9 +318,13 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     if (p->field_model == PIC_FIELD_POISSON) {
         ALLOC(B.ce, N);
         ALLOC(B.ca, N);
-        ALLOC(B.cx, N);
+        if (p->fine_solver == PIC_FINE_LAWSON_RK4) {
+            ALLOC(B.cxr, N);
+        } else {
+            ALLOC(B.cx, N);
+        }
         ALLOC(B.cj, N);
-        ALLOC(B.Qring, 3 * 2 * Np1);
+        ALLOC(B.Qring, 3 * 2 * Np1 * pic::kQPad);
         ALLOC(h->Qf, Np1);
         ALLOC(h->nout_f, 1);
         ALLOC(h->Ef, Np1);

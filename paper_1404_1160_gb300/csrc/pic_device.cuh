@@ -136,6 +136,37 @@ __device__ __forceinline__ Cell mesh_locate(const DevParams& P, double R) {
     return c;
 }
 
+// Exact-rounding int64 -> double (round to nearest, ties to even) with
+// integer instructions only; equal to (double)x for every int64.
+__device__ __forceinline__ double i64_to_double(long long x) {
+    if (x == 0) return 0.0;
+    const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+    unsigned long long m = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const int p = 63 - __clzll((long long)m);  // leading bit
+    int e = p;
+    if (p > 52) {
+        const int sh = p - 52;
+        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        m >>= sh;
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m >> 53) {  // carried into a new leading bit
+                m >>= 1;
+                ++e;
+            }
+        }
+    } else {
+        m <<= (52 - p);
+    }
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 1023) << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// x * 2^k for a normal x whose result stays normal (exponent arithmetic).
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+    if (x == 0.0) return x;
+    return __longlong_as_double(__double_as_longlong(x) + ((long long)k << 52));
+}
+
 // V > 0 for every non-NaN double, tested on the bit pattern (integer pipe).
 __device__ __forceinline__ bool positive(double v) { return __double_as_longlong(v) > 0; }
 
@@ -201,8 +232,9 @@ __device__ __forceinline__ double quad_root01(double v0, double v1, double v2) {
 
 // ------------------------------------------- per-particle period tracking
 
-// flags: bits 0-1 number of extrema seen, bit 2 resolved, bit 3 fallback.
-constexpr int F_NEXT = 3, F_RES = 4, F_FB = 8;
+// flags: bits 0-1 number of extrema seen, bit 2 resolved, bit 3 fallback,
+// bit 4 a sign change between the two previous samples awaits its root.
+constexpr int F_NEXT = 3, F_RES = 4, F_FB = 8, F_PEND = 16;
 
 struct Track {
     double t1, T, o;
@@ -253,6 +285,26 @@ __device__ __forceinline__ void track_sample(Track& s, const DevParams& P, int k
             } else {
                 track_resolve(s, P, T);
             }
+        }
+    }
+}
+
+// Root of an extremum already known to lie between samples k-2 and k-1,
+// from the stencil V_{k-2} = v0, V_{k-1} = v1, V_k = v2.
+__device__ __forceinline__ void track_root(Track& s, const DevParams& P, int k, double v0, double v1, double v2,
+                                           bool detect_only) {
+    if (s.flags & F_RES) return;
+    const double t = (double)(k - 2) + quad_root01(v0, v1, v2);
+    const int ne = (s.flags & F_NEXT) + 1;
+    s.flags = (s.flags & ~F_NEXT) | (ne & F_NEXT);
+    if (ne == 1) s.t1 = t;
+    if (ne == 3) {
+        const double T = t - s.t1;
+        if (detect_only) {
+            s.T = T;
+            s.flags |= F_RES;
+        } else {
+            track_resolve(s, P, T);
         }
     }
 }

@@ -43,21 +43,25 @@ cudaError_t launch_gather(const DevParams& P, const double* R, long long n, cons
 // interleaved so one 16-byte access moves both).
 struct WinBufs {
     double2* y;                 // current fine sample (R, V)
-    double* Vm2;                // V of the previous sample, for the sign test
     double *t1, *T, *o;         // first extremum, period, remainder (fine steps)
     int* N;                     // whole periods per macro step
     int2* tr;                   // (Track flags, last sample needed)
     double2* ce;                // values carried across a field cycle (fields / partial sums)
     double2* ca;                // W f (or R off the mesh) of the two deposited positions
-    int2* cj;                   // cells of the two deposited positions
-    double2* cx;                // Lawson: (Phi_h y)_R; RK4: stage positions
+    short2* cj;                 // cells of the two deposited positions (-1/-2 off the mesh)
+    double2* cx;                // RK4: stage positions carried across a cycle
+    double* cxr;                // Lawson: (Phi_h y)_R
     double2* traj;              // (Kmax+1) rows of n samples (R, V)
-    unsigned long long* Qring;  // 3 cycles x 2 fields x (n_cells+1)
+    unsigned long long* Qring;  // 3 cycles x 2 fields x (n_cells+1), one node per kQPad words
     int* notdone;               // 3 cycles
     unsigned int* bar;          // grid barrier: [0] arrivals, [32] released generation
     int* status;                // DEV_* of the launch
     long long* K_out;           // fine steps of the window
 };
+
+// Global charge of a node sits alone on a 128-byte line so the atomics of
+// all blocks spread over many L2 slices.
+constexpr int kQPad = 16;
 
 enum WindowMode { MODE_PERIODS = 0, MODE_ETD = 1, MODE_FINE = 2 };
 

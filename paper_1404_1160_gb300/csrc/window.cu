@@ -126,27 +126,35 @@ __device__ void block_exscan_pairs2(const long long* q, long long* g, int Nc, lo
 // Field tables of one cycle (two fields) from the cycle's global charge:
 // trapezoid integral from r = 0 (S_j = g_j - g_c), E_j = S_j q_unit/2 * (1/r_j),
 // E_c = Q_c q_unit / h_r, then (E_j, (E_{j+1}-E_j)/W) per cell.
-__device__ void build_fields(const DevParams& P, const unsigned long long* Qg, long long* q,
-                             long long* g, double2* tab, const double* inv_r, double* edges,
-                             long long* s_warp) {
+__device__ void build_fields(const DevParams& P, const unsigned long long* Qg, long long* q, long long* g,
+                             double2* tab, const double* inv_r, double* edges, long long* s_warp) {
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
-    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + idx);
+    for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + (size_t)idx * kQPad);
     __syncthreads();
     block_exscan_pairs2(q, g, Nc, s_warp);
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
         const long long S = g[idx] - g[f * Np1 + c];
+        // int64 -> double exactly as (double)S, on the integer pipe
+        const double Sd = i64_to_double(S);
         double e;
-        if (j == c) e = ((double)q[f * Np1 + c] * P.q_unit) * P.inv_hr;
-        else e = ((double)S * P.q_half) * inv_r[j];
+        if (j == c) e = (i64_to_double(q[f * Np1 + c]) * P.q_unit) * P.inv_hr;
+        else e = (Sd * P.q_half) * inv_r[j];
         tab[idx].x = e;
-        if (j == 0) edges[2 * f] = (double)S * P.q_half;
-        if (j == Nc) edges[2 * f + 1] = (double)S * P.q_half;
+        if (j == 0) edges[2 * f] = Sd * P.q_half;
+        if (j == Nc) edges[2 * f + 1] = Sd * P.q_half;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
-        tab[idx].y = (j < Nc) ? (tab[idx + 1].x - tab[idx].x) * P.invW : 0.0;
+        double sl = 0.0;
+        if (j < Nc) {
+            const double d = tab[idx + 1].x - tab[idx].x;
+            // d / W: exponent shift when the result stays normal (exact), else multiply
+            const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
+            sl = (ex > P.log2W + 1 && ex < 0x7ff) ? scale_pow2(d, -P.log2W) : d * P.invW;
+        }
+        tab[idx].y = sl;
     }
     __syncthreads();
 }
@@ -192,32 +200,37 @@ __device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar,
     return *s_ok != 0;
 }
 
-// Period tracking of one particle at sample k (k >= 1).  tr = (flags,
-// need) is loaded by the caller and updated here; the rarely used fields
-// are loaded lazily.  Returns true when the particle is done.
+// Period tracking of one particle at sample k (k >= 1), V_{k-1} = Vold,
+// V_k = Vnew.  A sign change between samples k-1 and k is marked pending
+// and its root taken at sample k+1 from V_{k-1}, V_k, V_{k+1} (V_{k-1} read
+// back from the trajectory store): the same crossings, stencils and order as
+// testing samples k-2, k-1 at sample k.  tr = (flags, need) is loaded by the
+// caller and updated here.  Returns true when the particle is done.
 __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& B, long long i, int k,
                                              double Vold, double Vnew, bool detect_only, int2& tr) {
-    const int fl = tr.x;
-    if (!(fl & F_RES)) {
+    if (!(tr.x & F_RES)) {
         Track s;
-        s.flags = fl;
+        s.flags = tr.x;
         s.t1 = 0.0;
         s.need = tr.y;
         bool touched = false;
-        if (k >= 2) {
-            const double v0 = B.Vm2[i];
-            if (positive(v0) != positive(Vold)) {
-                if ((fl & F_NEXT) >= 1) s.t1 = B.t1[i];
-                track_sample(s, P, k, v0, Vold, Vnew, detect_only);
-                touched = true;
-            }
+        if (s.flags & F_PEND) {
+            const double v0 = B.traj[(size_t)(k - 2) * P.n + i].y;
+            if ((s.flags & F_NEXT) >= 1) s.t1 = B.t1[i];
+            s.flags &= ~F_PEND;
+            track_root(s, P, k, v0, Vold, Vnew, detect_only);
+            if ((s.flags & F_NEXT) == 1 && !(tr.x & F_NEXT)) B.t1[i] = s.t1;
+            touched = true;
+        }
+        if (!(s.flags & F_RES) && positive(Vold) != positive(Vnew)) {
+            s.flags |= F_PEND;
+            touched = true;
         }
         if (k == P.Kmax) {
             track_cap(s, P, detect_only);
             touched = true;
         }
         if (touched) {
-            if ((s.flags & F_NEXT) == 1 && !(fl & F_NEXT)) B.t1[i] = s.t1;
             if (s.flags & F_RES) {
                 B.T[i] = s.T;
                 if (!detect_only) {
@@ -228,7 +241,6 @@ __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& 
             tr = make_int2(s.flags, (s.flags & F_RES) && !detect_only ? s.need : tr.y);
             B.tr[i] = tr;
         }
-        if (!(tr.x & F_RES)) B.Vm2[i] = Vold;
     }
     if (!(tr.x & F_RES)) return false;
     return detect_only || k >= tr.y;
@@ -242,15 +254,15 @@ template <int HIST>
 __device__ __forceinline__ void flush_hist(const DevParams& P, const WinBufs& B, const unsigned int* hist, int cyc) {
     const int Np1 = P.n_cells + 1;
     const int words = Hist<HIST>::kWordsPerNode * Np1;
-    unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1;
+    unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad;
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
         const unsigned long long v = hist_node<HIST>(hist + f * words, Np1, j, P.W);
-        if (v) atomicAdd(Qg + idx, v);
+        if (v) atomicAdd(Qg + (size_t)idx * kQPad, v);
     }
     if (blockIdx.x == 0) {
-        unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1;
-        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[idx] = 0ull;
+        unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1 * kQPad;
+        for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[(size_t)idx * kQPad] = 0ull;
     }
 }
 
@@ -273,9 +285,18 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
 
     const bool detect_only = mode == MODE_PERIODS, fine_only = mode == MODE_FINE;
     const long long n = P.n;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // Work unit: a chunk of 32 consecutive storage slots (phase-space
+    // neighbours after the sort) per warp.  Chunks go round-robin over the
+    // warps numbered warp-in-block major, so every block sees all phases
+    // (the sign changes of V spread evenly over blocks and fine steps) and
+    // the ragged remainder lands on one warp of many blocks, not on whole
+    // blocks.
     const int lane = threadIdx.x & 31;
+    const long long n_warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long g_warp = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const long long stride = n_warps * 32;
+    const long long i0 = g_warp * 32 + lane;
+    const long long s1 = n;
     const double ie = P.inv_eps, mie = P.mie;
     const long long W = P.W;
     unsigned int gen = 0;
@@ -283,7 +304,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     int K = 0;
 
     if (!fine_only) {
-        for (long long i = i0; i < n; i += stride) {
+        for (long long i = i0; i < s1; i += stride) {
             if (T_known) {
                 Track s;
                 s.flags = 0;
@@ -307,9 +328,9 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         const bool last_fine = fine_only && k == n_fine;
         unsigned int cnt = 0;
         // warp-uniform trip count: lanes past the end run with an empty cell
-        for (long long ib = i0 - lane; ib < n; ib += stride) {
+        for (long long ib = i0 - lane; ib < s1; ib += stride) {
             const long long i = ib + lane;
-            const bool valid = i < n;
+            const bool valid = i < s1;
             double R = 0.0, V = 0.0;
             if (valid) {
                 const double2 y = B.y[i];
@@ -318,8 +339,9 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             }
             if (!valid) {
             } else if (k > 0) {
-                const double2 ce = B.ce[i], ca = B.ca[i], cx = B.cx[i];
-                const int2 cj = B.cj[i];
+                const double2 ce = B.ce[i], ca = B.ca[i];
+                const double2 cx = SOLVER == 1 ? make_double2(B.cxr[i], 0.0) : B.cx[i];
+                const short2 cj = B.cj[i];
                 const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
                 const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
                 double Rn, Vn;
@@ -342,16 +364,18 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 }
                 if (!fine_only) {
                     int2 tr = B.tr[i];
+                    // the sample is stored before tracking: a pending root at
+                    // sample k+1 reads it back
+                    if (!((tr.x & F_RES) && (detect_only || k > tr.y)))
+                        __stcs(&B.traj[(size_t)k * n + i], make_double2(Rn, Vn));
                     const bool done = track_update(P, B, i, k, V, Vn, detect_only, tr);
-                    if (!detect_only && !((tr.x & F_RES) && k > tr.y))
-                        B.traj[(size_t)k * n + i] = make_double2(Rn, Vn);
                     cnt += done ? 0u : 1u;
                 }
                 R = Rn;
                 V = Vn;
                 B.y[i] = make_double2(R, V);
             } else if (!fine_only) {
-                if (!detect_only) B.traj[i] = make_double2(R, V);
+                __stcs(&B.traj[i], make_double2(R, V));
                 cnt += 1u;
             }
             if (last_fine) continue;
@@ -373,8 +397,9 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             deposit_cell<HIST>(hist + words, Np1, cb, W);
             if (valid) {
                 B.ca[i] = make_double2(ca.a, cb.a);
-                B.cj[i] = make_int2(ca.j, cb.j);
-                B.cx[i] = cx;
+                B.cj[i] = make_short2((short)ca.j, (short)cb.j);
+                if (SOLVER == 1) B.cxr[i] = cx.x;
+                else B.cx[i] = cx;
             }
         }
         if (last_fine) break;
@@ -395,21 +420,22 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 break;
             }
         }
-        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
+        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
         ++cyc;
 
         // ---- sweep B(k): gather pair 1, deposit stage pair 2
         for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
         __syncthreads();
-        for (long long ib = i0 - lane; ib < n; ib += stride) {
+        for (long long ib = i0 - lane; ib < s1; ib += stride) {
             const long long i = ib + lane;
-            const bool valid = i < n;
+            const bool valid = i < s1;
             double2 y = make_double2(0.0, 0.0), ca = make_double2(0.0, 0.0), cx = make_double2(0.0, 0.0);
-            int2 cj = make_int2(-3, -3);
+            short2 cj = make_short2(-3, -3);
             if (valid) {
                 y = B.y[i];
                 ca = B.ca[i];
-                cx = B.cx[i];
+                if (SOLVER == 1) cx.x = B.cxr[i];
+                else cx = B.cx[i];
                 cj = B.cj[i];
             }
             const double R = y.x, V = y.y;
@@ -442,13 +468,13 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             deposit_cell<HIST>(hist + words, Np1, cb2, W);
             if (valid) {
                 B.ca[i] = make_double2(ca2.a, cb2.a);
-                B.cj[i] = make_int2(ca2.j, cb2.j);
+                B.cj[i] = make_short2((short)ca2.j, (short)cb2.j);
             }
         }
         __syncthreads();
         flush_hist<HIST>(P, B, hist, cyc);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
-        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
+        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
         ++cyc;
     }
 
@@ -456,7 +482,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     if (mode != MODE_ETD) return;
 
     // ---- landing (step 3) and extrapolation (step 4)
-    for (long long i = i0; i < n; i += stride) {
+    for (long long i = i0; i < s1; i += stride) {
         const double o = B.o[i], T = B.T[i];
         const int N = B.N[i];
         double y[2][2];
@@ -695,7 +721,7 @@ cudaError_t window_prepare(const DevParams& P, int block, int blocks_per_sm, int
             bps = b < bps ? b : bps;
         }
     if (bps < 1) return cudaErrorInvalidConfiguration;
-    const int want = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    const int want = blocks_per_sm > 0 ? blocks_per_sm : 1;
     if (want < bps) bps = want;
     long long need = (P.n + block - 1) / block;
     long long grid = (long long)bps * sm_count;
