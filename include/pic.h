@@ -45,6 +45,7 @@ extern "C" {
 #define PIC_ERR_OVERFLOW      -4  /* n_particles * weight_fixed >= 2^62      */
 #define PIC_ERR_UNSUPPORTED   -5  /* valid request this build does not serve */
 #define PIC_ERR_NO_MEMORY     -6  /* device allocation failed                */
+#define PIC_ERR_TOO_LARGE     -7  /* beyond a fixed capacity (no-alloc call) */
 
 /* ---- enumerations ------------------------------------------------------ */
 enum { PIC_FIELD_POISSON = 0, PIC_FIELD_DUFFING = 1, PIC_FIELD_ZERO = 2 };
@@ -203,6 +204,23 @@ int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_
    on the stream. */
 int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
                 double* rE_edges_dev, void* stream);
+
+/* Same computation and arguments as pic_poisson, for callers that cannot
+   allocate device memory when they call it: for example code running inside
+   another framework that owns the device memory through its own caching
+   allocator, or a time-critical loop that must not stall on (or fail in) an
+   allocation.  The paper has no counterpart; it is a deployment variant.
+   Its scan scratch is a fixed array inside the library (136 KiB, enough for
+   n_cells <= 16384) that every GPU which loads the library keeps until the
+   process exits; larger meshes return PIC_ERR_TOO_LARGE and nothing runs.
+   It calls no device allocation or free.  The first call on each device
+   looks up the array's device address (so make that first call before any
+   stream capture).  All calls share the one array: each call clears the
+   parts that must start at zero, and calls whose work overlaps on the GPU
+   (different streams, or different host threads, without ordering between
+   them) race on it.  The call synchronises `stream` to read the status. */
+int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                        double* rE_edges_dev, void* stream);
 
 /* E at n positions R_dev by linear interpolation of E_dev with the deposit's
    weights; outside the mesh E = rE_edge / R (rE is constant beyond the

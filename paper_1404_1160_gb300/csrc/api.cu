@@ -259,6 +259,7 @@ const char* pic_strerror(int s) {
         case PIC_ERR_OVERFLOW: return "fixed-point charge would overflow (n*W >= 2^62)";
         case PIC_ERR_UNSUPPORTED: return "unsupported request";
         case PIC_ERR_NO_MEMORY: return "device memory allocation failed";
+        case PIC_ERR_TOO_LARGE: return "size exceeds the fixed scratch capacity of a no-allocation entry point";
         default: return "unknown status";
     }
 }
@@ -619,16 +620,36 @@ int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_
                                         (cudaStream_t)stream, sms, nullptr));
 }
 
-int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
-                double* rE_edges_dev, void* stream) {
+}  // extern "C"
+
+// Shared body of pic_poisson and pic_poisson_noalloc: S is the caller's
+// scratch (flags, tile counter and status are cleared here, on the stream).
+int pic::poisson_with_scratch(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                              double* rE_edges_dev, const pic::ScanScratch* S, void* stream) {
     int rc = check_params(p, true);
     if (rc) return rc;
-    if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
+    if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev || !S) return PIC_ERR_INVALID_ARG;
     if ((double)n_particles * (double)p->weight_fixed >= 4.611686018427388e18) return PIC_ERR_OVERFLOW;
     int sms = 0;
     if ((rc = current_sm_count(&sms))) return rc;
     DevParams d;
     make_devparams(p, n_particles, &d);
+    cudaStream_t st = (cudaStream_t)stream;
+    int status = 0;
+    cudaError_t e = pic::launch_poisson(d, (const long long*)Q_dev, E_dev, rE_edges_dev, *S, st, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, S->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return map_cuda(e);
+    return map_dev(status);
+}
+
+extern "C" {
+
+int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                double* rE_edges_dev, void* stream) {
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int tiles = (p->n_cells + pic::kScanTile - 1) / pic::kScanTile;
     const size_t bytes = pic::scan_scratch_layout(p->n_cells, tiles, nullptr, nullptr);
@@ -637,14 +658,10 @@ int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, 
     if (e != cudaSuccess) return map_cuda(e);
     pic::ScanScratch S;
     pic::scan_scratch_layout(p->n_cells, tiles, mem, &S);
-    int status = 0;
-    e = pic::launch_poisson(d, (const long long*)Q_dev, E_dev, rE_edges_dev, S, st, nullptr);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, S.status, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaError_t e2 = cudaFreeAsync(mem, st);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return map_cuda(e);
-    return map_dev(status);
+    rc = pic::poisson_with_scratch(p, n_particles, Q_dev, E_dev, rE_edges_dev, &S, stream);
+    e = cudaFreeAsync(mem, st);
+    if (rc == PIC_OK && e != cudaSuccess) rc = map_cuda(e);
+    return rc;
 }
 
 int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double* E_dev,

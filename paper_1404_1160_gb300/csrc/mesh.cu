@@ -1,6 +1,9 @@
 // mesh.cu -- standalone field-cycle kernels: CIC deposit, trapezoid prefix
 // integral (decoupled look-back int64 scan) and gather (Sec. 2.3 of Frenod,
 // Hirstoaga & Lutz; eq. VlasPoissAxSymBeam).
+#include <mutex>
+
+#include "pic.h"
 #include "pic_device.cuh"
 #include "pic_internal.h"
 
@@ -314,3 +317,46 @@ cudaError_t launch_gather(const DevParams& P, const double* R, long long n, cons
 }
 
 }  // namespace pic
+
+// ----------------------------------------------- scan without allocation
+
+namespace pic {
+
+// Fixed device scratch for pic_poisson_noalloc: the look-back tile states,
+// the prefix G and the status word of one scan of at most
+// kNoAllocMaxCells cells.  Every GPU that loads the library holds it until
+// the process exits.
+constexpr int kNoAllocMaxCells = 16384;
+constexpr size_t kNoAllocScratchBytes = 136 * 1024;
+static __device__ __align__(256) unsigned char g_poisson_scratch[kNoAllocScratchBytes];
+
+}  // namespace pic
+
+extern "C" int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                                   double* rE_edges_dev, void* stream) {
+    // Host code cannot use g_poisson_scratch's name as a device address: the
+    // address is looked up once per device (with that device current) and
+    // cached.  This set-up happens in the first call on each device.
+    static std::mutex mu;
+    static void* scratch_addr[256] = {};
+    if (!p) return PIC_ERR_INVALID_ARG;
+    if (p->n_cells > pic::kNoAllocMaxCells) return PIC_ERR_TOO_LARGE;
+    if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return PIC_ERR_CUDA;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!scratch_addr[dev]) {
+            void* a = nullptr;
+            if (cudaGetSymbolAddress(&a, pic::g_poisson_scratch) != cudaSuccess || !a) return PIC_ERR_CUDA;
+            scratch_addr[dev] = a;
+        }
+        base = scratch_addr[dev];
+    }
+    const int tiles = (p->n_cells + pic::kScanTile - 1) / pic::kScanTile;
+    if (pic::scan_scratch_layout(p->n_cells, tiles, nullptr, nullptr) > pic::kNoAllocScratchBytes) return PIC_ERR_TOO_LARGE;
+    pic::ScanScratch S;
+    pic::scan_scratch_layout(p->n_cells, tiles, base, &S);
+    return pic::poisson_with_scratch(p, n_particles, Q_dev, E_dev, rE_edges_dev, &S, stream);
+}

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "pic.h"
 #include "pic_device.cuh"
 
 namespace pic {
@@ -114,4 +115,10 @@ constexpr int kMomInts = 3;      // minN maxN n_fallback
 cudaError_t launch_moments(const DevParams& P, const WinBufs& B, double* part_d,
                            long long* part_i, int grid, cudaStream_t st, long long* launches);
 
+}  // namespace pic
+
+namespace pic {
+// Poisson prefix integral on caller-provided scan scratch (api.cu).
+int poisson_with_scratch(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
+                         double* rE_edges_dev, const ScanScratch* S, void* stream);
 }  // namespace pic

@@ -25,6 +25,7 @@ PIC_ERR_TIMEOUT = -3
 PIC_ERR_OVERFLOW = -4
 PIC_ERR_UNSUPPORTED = -5
 PIC_ERR_NO_MEMORY = -6
+PIC_ERR_TOO_LARGE = -7
 
 PIC_FIELD_POISSON, PIC_FIELD_DUFFING, PIC_FIELD_ZERO = 0, 1, 2
 PIC_FINE_RK4, PIC_FINE_LAWSON_RK4 = 0, 1
@@ -129,6 +130,7 @@ def load() -> C.CDLL:
             "pic_strerror": (C.c_char_p, [i32]),
             "pic_deposit": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_poisson": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
+            "pic_poisson_noalloc": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
             "pic_test_barrier_timeout": (i32, [i64, vp]),
         }
@@ -304,6 +306,12 @@ def pic_deposit(params: pic_params, R_dev, Q_dev, n_out_dev, stream=None) -> Non
 
 def pic_poisson(params: pic_params, n_particles: int, Q_dev, E_dev, edges_dev, stream=None) -> None:
     _check(load().pic_poisson(C.byref(params), n_particles, _ptr(Q_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _stream(stream)), "pic_poisson")
+
+
+def pic_poisson_noalloc(params: pic_params, n_particles: int, Q_dev, E_dev, edges_dev, stream=None) -> int:
+    """Returns the raw status (this call is also tested for its size limit)."""
+    return int(load().pic_poisson_noalloc(C.byref(params), n_particles, _ptr(Q_dev)[0], _ptr(E_dev)[0],
+                                          _ptr(edges_dev)[0], _stream(stream)))
 
 
 def pic_gather(params: pic_params, R_dev, E_dev, edges_dev, e_dev, stream=None) -> None:
