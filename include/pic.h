@@ -137,6 +137,9 @@ typedef struct {
     int64_t N_min, N_max;      /* whole periods per macro step, last step       */
     int64_t window_steps;      /* fine steps in the last window                 */
     int64_t n_no_period;       /* particles that took T = 2*pi*eps last step    */
+    double  window_ms;         /* device time of the window kernel launches of
+                                  the last pic_step call (CUDA events)         */
+    int64_t window_launches;   /* window kernel launches of that call           */
 } pic_moments_t;
 
 /* Diagnostics of the current state (computed by device reductions; one small
@@ -169,6 +172,10 @@ typedef struct {
 } pic_state_t;
 int pic_get_state(pic_handle* h, pic_state_t* out);
 int pic_set_state(pic_handle* h, const pic_state_t* in);
+
+/* Device time (CUDA events on the handle's stream) of the window kernel
+   launches of the last pic_step call, and their number.  Host only. */
+int pic_window_time(const pic_handle* h, double* ms, int64_t* launches);
 
 int64_t pic_num_particles(const pic_handle* h);
 void pic_destroy(pic_handle* h);

@@ -153,6 +153,10 @@ struct pic_handle {
     long long n_steps = 0;
     int have_periods = 0;
     long long launches = 0;
+    // CUDA events around the window launches of the last pic_step call
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double window_ms = 0.0;
 };
 
 namespace {
@@ -172,6 +176,8 @@ int dalloc(pic_handle* h, T** p, size_t count) {
 void free_all(pic_handle* h) {
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
     if (h->status_host) cudaFreeHost(h->status_host);
     h->status_host = nullptr;
 }
@@ -193,6 +199,28 @@ cudaError_t reset_coop(pic_handle* h) {
     return e;
 }
 
+// Grows the pool of timing events to at least `count`.
+cudaError_t ensure_events(pic_handle* h, int count) {
+    if (count > 256) return cudaErrorNotReady;  // stop timing, not the step
+    while ((int)h->ev.size() < count) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        h->ev.push_back(e);
+    }
+    return cudaSuccess;
+}
+
+// Sum of the timed window launches (after the stream has been synchronised).
+void collect_window_ms(pic_handle* h) {
+    double ms = 0.0;
+    for (int k = 0; k + 1 < h->ev_used; k += 2) {
+        float x = 0.f;
+        if (cudaEventElapsedTime(&x, h->ev[k], h->ev[k + 1]) == cudaSuccess) ms += x;
+    }
+    h->window_ms = ms;
+}
+
 // Phase-space sort of the storage order before a window (see sort.cu).
 cudaError_t maybe_sort(pic_handle* h, long long step_index) {
     if (h->prm.sort_every <= 0 || step_index % h->prm.sort_every != 0) return cudaSuccess;
@@ -204,14 +232,21 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     cudaError_t e = cudaMemsetAsync(h->B.status, 0, sizeof(int), h->st);
     if (e != cudaSuccess) return map_cuda(e);
     const int T_known = (mode == pic::MODE_ETD && h->prm.periods_once) ? 1 : 0;
+    h->ev_used = 0;
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         const long long reps = mode == pic::MODE_ETD ? n_iter : 1;
         for (long long s = 0; s < reps && e == cudaSuccess; ++s) {
             if (mode == pic::MODE_ETD) e = maybe_sort(h, h->n_steps + s);
             if (e == cudaSuccess) e = reset_coop(h);
+            const bool timed = e == cudaSuccess && ensure_events(h, h->ev_used + 2) == cudaSuccess;
+            if (timed) cudaEventRecord(h->ev[h->ev_used], h->st);
             if (e == cudaSuccess)
                 e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, mode == pic::MODE_FINE ? n_iter : 0,
                                             h->st, &h->launches, h->Tin);
+            if (timed) {
+                cudaEventRecord(h->ev[h->ev_used + 1], h->st);
+                h->ev_used += 2;
+            }
         }
     } else {
         if (mode == pic::MODE_ETD) e = maybe_sort(h, 0);
@@ -221,7 +256,9 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
                                          h->block, h->sm_count, h->st, &h->launches, h->Tin);
     }
     if (e != cudaSuccess) return map_cuda(e);
-    return read_status(h);
+    const int rc = read_status(h);
+    collect_window_ms(h);
+    return rc;
 }
 
 }  // namespace
@@ -482,6 +519,8 @@ int pic_moments(pic_handle* h, pic_moments_t* out) {
         out->n_no_period = b[2];
         out->window_steps = Kw;
     }
+    out->window_ms = h->window_ms;
+    out->window_launches = h->ev_used / 2;
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         std::vector<int64_t> Q((size_t)h->dp.n_cells + 1);
         int64_t nout = 0;
@@ -591,6 +630,13 @@ int pic_set_state(pic_handle* h, const pic_state_t* in) {
     if (e != cudaSuccess) return map_cuda(e);
     h->t = in->t;
     h->n_steps = in->n_steps;
+    return PIC_OK;
+}
+
+int pic_window_time(const pic_handle* h, double* ms, int64_t* launches) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    if (ms) *ms = h->window_ms;
+    if (launches) *launches = h->ev_used / 2;
     return PIC_OK;
 }
 

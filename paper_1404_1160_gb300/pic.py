@@ -81,6 +81,8 @@ class pic_moments_t(C.Structure):
         ("N_max", C.c_int64),
         ("window_steps", C.c_int64),
         ("n_no_period", C.c_int64),
+        ("window_ms", C.c_double),
+        ("window_launches", C.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -125,6 +127,7 @@ def load() -> C.CDLL:
             "pic_get_state": (i32, [H, P(pic_state_t)]),
             "pic_set_state": (i32, [H, P(pic_state_t)]),
             "pic_num_particles": (i64, [H]),
+            "pic_window_time": (i32, [H, P(d), P(i64)]),
             "pic_launch_count": (i64, [H]),
             "pic_destroy": (None, [H]),
             "pic_strerror": (C.c_char_p, [i32]),
@@ -286,6 +289,14 @@ def pic_set_state(h: Handle, state: dict) -> None:
     pd = C.POINTER(C.c_double)
     st = pic_state_t(r.ctypes.data_as(pd), v.ctypes.data_as(pd), T.ctypes.data_as(pd), float(state["t"]), int(state["n_steps"]))
     _check(load().pic_set_state(h.ptr, C.byref(st)), "pic_set_state")
+
+
+def pic_window_time(h: Handle):
+    """(device ms, launches) of the window kernels of the last pic_step call."""
+    ms = C.c_double()
+    k = C.c_int64()
+    _check(load().pic_window_time(h.ptr, C.byref(ms), C.byref(k)), "pic_window_time")
+    return ms.value, k.value
 
 
 def pic_num_particles(h: Handle) -> int:
