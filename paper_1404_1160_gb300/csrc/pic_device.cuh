@@ -44,6 +44,7 @@ struct DevParams {
     long long n;                       // particles
     long long wait_ns;                 // limit of device-side waits
     int bar_extra;                     // testing only: arrivals a barrier waits for beyond the grid
+    int hist_copies;                   // copies of each block's charge histogram (window kernel)
 };
 
 // ---------------------------------------------------------------- mesh

@@ -69,10 +69,12 @@ enum WindowMode { MODE_PERIODS = 0, MODE_ETD = 1, MODE_FINE = 2 };
 struct WindowLaunch {
     int coop_grid = 0, coop_block = 0;
     int hist = 0;             // 0: 32-bit split histograms, 1: 64-bit
+    int stage = 0;            // 1: cp.async staging of each warp's next chunk
     size_t coop_smem = 0;
 };
 
-cudaError_t window_prepare(const DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L);
+// Picks the launch shape and the number of histogram copies (P.hist_copies).
+cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L);
 // Poisson: one cooperative persistent launch per macro step (or per fine run).
 cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L,
                                int mode, int T_known, long long n_fine, cudaStream_t st,

@@ -21,6 +21,7 @@
 namespace pic {
 
 constexpr int kWinMaxThreads = 1024;
+constexpr int kHistCopiesMax = 2;
 
 // ---------------------------------------------------------------- helpers
 
@@ -56,15 +57,24 @@ __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cel
     }
 }
 
+// Node charge of one field from the block histogram, summed over its
+// `copies` copies `stride` words apart (warp w deposits into copy
+// w % copies, so a hot cell at the beam centre is updated on several
+// addresses instead of one).
 template <int HIST>
-__device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, int Np1, int j, long long W) {
+__device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, int Np1, int j, long long W, int stride,
+                                                        int copies) {
     if (HIST == 0) {
-        auto S = [&](int m) -> unsigned long long {
-            return m < 0 || m >= Np1 - 1 ? 0ull
-                                         : ((unsigned long long)h[2 * Np1 + m] << 16) + (unsigned long long)h[Np1 + m];
-        };
-        const unsigned long long C = (j < Np1 - 1) ? (unsigned long long)h[j] : 0ull;
-        return C * (unsigned long long)W - S(j) + S(j - 1);
+        unsigned long long C = 0, Sj = 0, Sm = 0;
+        for (int c = 0; c < copies; ++c) {
+            const unsigned int* hc = h + c * stride;
+            if (j < Np1 - 1) {
+                C += hc[j];
+                Sj += ((unsigned long long)hc[2 * Np1 + j] << 16) + (unsigned long long)hc[Np1 + j];
+            }
+            if (j >= 1) Sm += ((unsigned long long)hc[2 * Np1 + j - 1] << 16) + (unsigned long long)hc[Np1 + j - 1];
+        }
+        return C * (unsigned long long)W - Sj + Sm;
     } else {
         return ((const unsigned long long*)h)[j];
     }
@@ -74,7 +84,7 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, x, d);
+        const long long y = __shfl_up_sync(0xffffffffu, x, d);
         if (lane >= d) x += y;
     }
     return x;
@@ -257,7 +267,7 @@ __device__ __forceinline__ void flush_hist(const DevParams& P, const WinBufs& B,
     unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad;
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
-        const unsigned long long v = hist_node<HIST>(hist + f * words, Np1, j, P.W);
+        const unsigned long long v = hist_node<HIST>(hist + f * words, Np1, j, P.W, 2 * words, P.hist_copies);
         if (v) atomicAdd(Qg + (size_t)idx * kQPad, v);
     }
     if (blockIdx.x == 0) {
@@ -266,19 +276,102 @@ __device__ __forceinline__ void flush_hist(const DevParams& P, const WinBufs& B,
     }
 }
 
-template <int SOLVER, int HIST, int POW2>
+// ---- asynchronous staging of a warp's next chunk (cp.async, sm_80+)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One chunk (32 particles) of window state in shared memory; lane l owns
+// entry l of every array, so no warp synchronisation is needed.
+struct Stage {
+    double2 y[32];
+    double2 ce[32];
+    double2 ca[32];
+    double2 cx[32];  // Lawson uses .x ((Phi_h y)_R), RK4 both stage positions
+    int2 tr[32];
+    short2 cj[32];
+};
+constexpr size_t kStageBytesPerWarp = 2 * sizeof(Stage);
+
+// The state a sweep reads for one particle.
+struct ChunkIn {
+    double2 y, ce, ca, cx;
+    int2 tr;
+    short2 cj;
+};
+
+template <int SOLVER>
+__device__ __forceinline__ void prefetch_chunk(const WinBufs& B, long long i, bool sweepA, bool fine_only, bool k0,
+                                               Stage* s, int lane) {
+    cp_async16(&s->y[lane], &B.y[i]);
+    if (sweepA && !fine_only) cp_async8(&s->tr[lane], &B.tr[i]);
+    if (sweepA && k0) return;
+    if (sweepA) cp_async16(&s->ce[lane], &B.ce[i]);
+    cp_async16(&s->ca[lane], &B.ca[i]);
+    if (SOLVER == 1) cp_async8(&s->cx[lane].x, &B.cxr[i]);
+    else cp_async16(&s->cx[lane], &B.cx[i]);
+    cp_async4(&s->cj[lane], &B.cj[i]);
+}
+
+template <int SOLVER>
+__device__ __forceinline__ ChunkIn load_chunk(const WinBufs& B, long long i, bool sweepA, bool fine_only, bool k0) {
+    ChunkIn c;
+    c.y = B.y[i];
+    c.tr = (sweepA && !fine_only) ? B.tr[i] : make_int2(0, 0);
+    c.ce = make_double2(0.0, 0.0);
+    c.ca = make_double2(0.0, 0.0);
+    c.cx = make_double2(0.0, 0.0);
+    c.cj = make_short2(-3, -3);
+    if (sweepA && k0) return c;
+    if (sweepA) c.ce = B.ce[i];
+    c.ca = B.ca[i];
+    if (SOLVER == 1) c.cx.x = B.cxr[i];
+    else c.cx = B.cx[i];
+    c.cj = B.cj[i];
+    return c;
+}
+
+__device__ __forceinline__ ChunkIn read_stage(const Stage* s, int lane) {
+    ChunkIn c;
+    c.y = s->y[lane];
+    c.ce = s->ce[lane];
+    c.ca = s->ca[lane];
+    c.cx = s->cx[lane];
+    c.tr = s->tr[lane];
+    c.cj = s->cj[lane];
+    return c;
+}
+
+template <int SOLVER, int HIST, int POW2, int STAGE>
 __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, WinBufs B, int mode, int T_known,
                                                                 long long n_fine, const double* __restrict__ Tin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Nc = P.n_cells, Np1 = Nc + 1;
     const int words = Hist<HIST>::kWordsPerNode * Np1;   // 32-bit words per field histogram
-    double2* tab = (double2*)smem_raw;                    // 2 Np1
-    unsigned int* hist = (unsigned int*)(tab + 2 * Np1);  // 2 fields x words (also the scan input)
-    long long* g = (long long*)(hist + 2 * 3 * Np1);      // 2 Np1
+    const int copies = P.hist_copies;
+    Stage* stage = (Stage*)smem_raw;                      // STAGE: 2 per warp
+    double2* tab = (double2*)(smem_raw + (STAGE ? (blockDim.x >> 5) * kStageBytesPerWarp : 0));  // 2 Np1
+    unsigned int* hist = (unsigned int*)(tab + 2 * Np1);  // copies x 2 fields x words (also the scan input)
+    long long* g = (long long*)(hist + (copies > 2 ? copies : 2) * 2 * 3 * Np1);  // 2 Np1
     double* inv_r = (double*)(g + 2 * Np1);               // Np1
     __shared__ double s_edges[4];
     __shared__ long long s_warp[64];
-    __shared__ int s_ok, s_cnt, s_stop;
+    __shared__ int s_ok, s_cnt, s_stop, s_next;
 
     for (int j = threadIdx.x; j < Np1; j += blockDim.x)
         inv_r[j] = (j == P.c) ? 0.0 : 1.0 / (P.r_min + (double)j * P.hr);
@@ -286,17 +379,26 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     const bool detect_only = mode == MODE_PERIODS, fine_only = mode == MODE_FINE;
     const long long n = P.n;
     // Work unit: a chunk of 32 consecutive storage slots (phase-space
-    // neighbours after the sort) per warp.  Chunks go round-robin over the
-    // warps numbered warp-in-block major, so every block sees all phases
-    // (the sign changes of V spread evenly over blocks and fine steps) and
-    // the ragged remainder lands on one warp of many blocks, not on whole
-    // blocks.
+    // neighbours after the sort).  Block b owns the chunks c = b (mod grid),
+    // so every block sees all phases (the sign changes of V spread evenly
+    // over blocks and fine steps) and a slot always stays on one SM; inside
+    // the block, warps take the block's chunks dynamically from a shared
+    // counter, so they finish a sweep together.
     const int lane = threadIdx.x & 31;
+    const long long n_chunks = (n + 31) / 32;
+    unsigned int* const my_hist = hist + ((threadIdx.x >> 5) % copies) * 2 * words;
+    Stage* const my_stage = stage + 2 * (threadIdx.x >> 5);
     const long long n_warps = (long long)gridDim.x * (blockDim.x >> 5);
     const long long g_warp = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const long long stride = n_warps * 32;
+    const long long stride = n_warps * 32;  // static mapping (init and landing)
     const long long i0 = g_warp * 32 + lane;
-    const long long s1 = n;
+    // next chunk of this block for this warp (warp-uniform)
+    auto grab = [&]() -> long long {
+        int m = 0;
+        if (lane == 0) m = atomicAdd(&s_next, 1);
+        m = __shfl_sync(0xffffffffu, m, 0);
+        return (long long)blockIdx.x + (long long)m * gridDim.x;
+    };
     const double ie = P.inv_eps, mie = P.mie;
     const long long W = P.W;
     unsigned int gen = 0;
@@ -304,7 +406,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     int K = 0;
 
     if (!fine_only) {
-        for (long long i = i0; i < s1; i += stride) {
+        for (long long i = i0; i < n; i += stride) {
             if (T_known) {
                 Track s;
                 s.flags = 0;
@@ -322,48 +424,61 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
 
     for (int k = 0;; ++k) {
         // ---- sweep A(k): finish step k-1, sample k, deposit stage pair 1 of step k
-        for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
-        if (threadIdx.x == 0) s_cnt = 0;
+        for (int idx = threadIdx.x; idx < copies * 2 * words; idx += blockDim.x) hist[idx] = 0u;
+        if (threadIdx.x == 0) {
+            s_cnt = 0;
+            s_next = 0;
+        }
         __syncthreads();
         const bool last_fine = fine_only && k == n_fine;
+        const bool k0 = k == 0;
         unsigned int cnt = 0;
+        int cur = 0;
+        long long c = grab();
+        if (STAGE) {
+            if (c < n_chunks && c * 32 + lane < n) prefetch_chunk<SOLVER>(B, c * 32 + lane, true, fine_only, k0, my_stage, lane);
+            cp_async_commit();
+        }
         // warp-uniform trip count: lanes past the end run with an empty cell
-        for (long long ib = i0 - lane; ib < s1; ib += stride) {
-            const long long i = ib + lane;
-            const bool valid = i < s1;
-            double R = 0.0, V = 0.0;
-            if (valid) {
-                const double2 y = B.y[i];
-                R = y.x;
-                V = y.y;
+        for (; c < n_chunks; cur ^= 1) {
+            const long long cn = grab();
+            const long long i = c * 32 + lane;
+            const bool valid = i < n;
+            ChunkIn in;
+            if (STAGE) {
+                if (cn < n_chunks && cn * 32 + lane < n) prefetch_chunk<SOLVER>(B, cn * 32 + lane, true, fine_only, k0, my_stage + (cur ^ 1), lane);
+                cp_async_commit();
+                cp_async_wait<1>();
+                in = read_stage(my_stage + cur, lane);
+            } else if (valid) {
+                in = load_chunk<SOLVER>(B, i, true, fine_only, k0);
             }
+            c = cn;
+            double R = valid ? in.y.x : 0.0, V = valid ? in.y.y : 0.0;
             if (!valid) {
             } else if (k > 0) {
-                const double2 ce = B.ce[i], ca = B.ca[i];
-                const double2 cx = SOLVER == 1 ? make_double2(B.cxr[i], 0.0) : B.cx[i];
-                const short2 cj = B.cj[i];
-                const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
-                const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
+                const double ea = mesh_gather(tab, s_edges[0], s_edges[1], in.cj.x, in.ca.x);
+                const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], in.cj.y, in.ca.y);
                 double Rn, Vn;
                 if (SOLVER == 1) {
                     // ce = (e1, e3), ea = e2, eb = e4, cx.x = (Phi_h y)_R
-                    const double e1 = ce.x, e3 = ce.y;
+                    const double e1 = in.ce.x, e3 = in.ce.y;
                     const double Bv = fma(P.c1, V, -(P.s1 * R));
                     const double e23 = ea + e3;
-                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), cx.x);
+                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), in.cx.x);
                     Vn = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, eb)), Bv);
                 } else {
                     // ce = partial sums, cx = (R3, R4), ea = e3, eb = e4
-                    const double k3V = fma(mie, cx.x, ea);
+                    const double k3V = fma(mie, in.cx.x, ea);
                     const double V4 = fma(P.h, k3V, V);
-                    const double k4R = ie * V4, k4V = fma(mie, cx.y, eb);
-                    const double sR = ce.x + k4R;
-                    const double sV = (ce.y + 2.0 * k3V) + k4V;
+                    const double k4R = ie * V4, k4V = fma(mie, in.cx.y, eb);
+                    const double sR = in.ce.x + k4R;
+                    const double sV = (in.ce.y + 2.0 * k3V) + k4V;
                     Rn = fma(P.h6, sR, R);
                     Vn = fma(P.h6, sV, V);
                 }
                 if (!fine_only) {
-                    int2 tr = B.tr[i];
+                    int2 tr = in.tr;
                     // the sample is stored before tracking: a pending root at
                     // sample k+1 reads it back
                     if (!((tr.x & F_RES) && (detect_only || k > tr.y)))
@@ -393,8 +508,8 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 cx = make_double2(R2, 0.0);
             }
             if (!valid) ca.j = cb.j = -3;
-            deposit_cell<HIST>(hist, Np1, ca, W);
-            deposit_cell<HIST>(hist + words, Np1, cb, W);
+            deposit_cell<HIST>(my_hist, Np1, ca, W);
+            deposit_cell<HIST>(my_hist + words, Np1, cb, W);
             if (valid) {
                 B.ca[i] = make_double2(ca.a, cb.a);
                 B.cj[i] = make_short2((short)ca.j, (short)cb.j);
@@ -402,6 +517,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 else B.cx[i] = cx;
             }
         }
+        if (STAGE) cp_async_wait<0>();
         if (last_fine) break;
         if (!fine_only) {
             cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -424,34 +540,49 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         ++cyc;
 
         // ---- sweep B(k): gather pair 1, deposit stage pair 2
-        for (int idx = threadIdx.x; idx < 2 * words; idx += blockDim.x) hist[idx] = 0u;
+        for (int idx = threadIdx.x; idx < copies * 2 * words; idx += blockDim.x) hist[idx] = 0u;
+        if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
-        for (long long ib = i0 - lane; ib < s1; ib += stride) {
-            const long long i = ib + lane;
-            const bool valid = i < s1;
-            double2 y = make_double2(0.0, 0.0), ca = make_double2(0.0, 0.0), cx = make_double2(0.0, 0.0);
-            short2 cj = make_short2(-3, -3);
-            if (valid) {
-                y = B.y[i];
-                ca = B.ca[i];
-                if (SOLVER == 1) cx.x = B.cxr[i];
-                else cx = B.cx[i];
-                cj = B.cj[i];
+        cur = 0;
+        c = grab();
+        if (STAGE) {
+            if (c < n_chunks && c * 32 + lane < n) prefetch_chunk<SOLVER>(B, c * 32 + lane, false, fine_only, false, my_stage, lane);
+            cp_async_commit();
+        }
+        for (; c < n_chunks; cur ^= 1) {
+            const long long cn = grab();
+            const long long i = c * 32 + lane;
+            const bool valid = i < n;
+            ChunkIn in;
+            if (STAGE) {
+                if (cn < n_chunks && cn * 32 + lane < n) prefetch_chunk<SOLVER>(B, cn * 32 + lane, false, fine_only, false, my_stage + (cur ^ 1), lane);
+                cp_async_commit();
+                cp_async_wait<1>();
+                in = read_stage(my_stage + cur, lane);
+            } else if (valid) {
+                in = load_chunk<SOLVER>(B, i, false, fine_only, false);
             }
-            const double R = y.x, V = y.y;
-            const double ea = mesh_gather(tab, s_edges[0], s_edges[1], cj.x, ca.x);
-            const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], cj.y, ca.y);
+            c = cn;
+            if (!valid) {
+                in.y = make_double2(0.0, 0.0);
+                in.ca = make_double2(0.0, 0.0);
+                in.cx = make_double2(0.0, 0.0);
+                in.cj = make_short2(-3, -3);
+            }
+            const double R = in.y.x, V = in.y.y;
+            const double ea = mesh_gather(tab, s_edges[0], s_edges[1], in.cj.x, in.ca.x);
+            const double eb = mesh_gather(tab + Np1, s_edges[2], s_edges[3], in.cj.y, in.ca.y);
             double Pa, Pb;
             if (SOLVER == 1) {
                 // ea = e1 at y, eb = e3 at Phi_h/2 y
                 Pa = fma(P.sh, fma(P.h2, ea, V), P.ch * R);              // stage 2
-                Pb = fma(P.hsh, eb, cx.x);                               // stage 4
+                Pb = fma(P.hsh, eb, in.cx.x);                            // stage 4
                 if (valid) B.ce[i] = make_double2(ea, eb);
             } else {
                 // ea = e1 at y, eb = e2 at y + h/2 k1, cx.x = R2
                 const double k1R = ie * V, k1V = fma(mie, R, ea);
                 const double V2 = fma(P.h2, k1V, V);
-                const double k2R = ie * V2, k2V = fma(mie, cx.x, eb);
+                const double k2R = ie * V2, k2V = fma(mie, in.cx.x, eb);
                 const double R3 = fma(P.h2, k2R, R), V3 = fma(P.h2, k2V, V);
                 const double k3R = ie * V3;
                 const double R4 = fma(P.h, k3R, R);
@@ -464,13 +595,14 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             }
             Cell ca2 = mesh_locate<POW2>(P, Pa), cb2 = mesh_locate<POW2>(P, Pb);
             if (!valid) ca2.j = cb2.j = -3;
-            deposit_cell<HIST>(hist, Np1, ca2, W);
-            deposit_cell<HIST>(hist + words, Np1, cb2, W);
+            deposit_cell<HIST>(my_hist, Np1, ca2, W);
+            deposit_cell<HIST>(my_hist + words, Np1, cb2, W);
             if (valid) {
                 B.ca[i] = make_double2(ca2.a, cb2.a);
                 B.cj[i] = make_short2((short)ca2.j, (short)cb2.j);
             }
         }
+        if (STAGE) cp_async_wait<0>();
         __syncthreads();
         flush_hist<HIST>(P, B, hist, cyc);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
@@ -482,7 +614,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     if (mode != MODE_ETD) return;
 
     // ---- landing (step 3) and extrapolation (step 4)
-    for (long long i = i0; i < s1; i += stride) {
+    for (long long i = i0; i < n; i += stride) {
         const double o = B.o[i], T = B.T[i];
         const int N = B.N[i];
         double y[2][2];
@@ -691,52 +823,68 @@ __global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* par
 
 // ------------------------------------------------------------- launchers
 
-static size_t coop_smem_bytes(int n_cells) {
+// Shared memory of the window kernel with `copies` histogram copies (at
+// least two copies' worth: the histogram region doubles as the int64 scan
+// input) and, with staging, two Stage buffers per warp.
+static size_t coop_smem_bytes(int n_cells, int copies, int block, int stage) {
     const size_t Np1 = (size_t)n_cells + 1;
-    return 2 * Np1 * sizeof(double2) + 2 * 3 * Np1 * sizeof(unsigned int) + 2 * Np1 * sizeof(long long) +
-           Np1 * sizeof(double);
+    const size_t hc = (size_t)(copies > 2 ? copies : 2);
+    return (stage ? (size_t)(block / 32) * kStageBytesPerWarp : 0) + 2 * Np1 * sizeof(double2) +
+           hc * 2 * 3 * Np1 * sizeof(unsigned int) + 2 * Np1 * sizeof(long long) + Np1 * sizeof(double);
 }
 
-static void* coop_fn(int solver, int hist, int pow2) {
+template <int SOLVER, int HIST, int POW2>
+static void* coop_fn3(int stage) {
+    return stage ? (void*)k_window_coop<SOLVER, HIST, POW2, 1> : (void*)k_window_coop<SOLVER, HIST, POW2, 0>;
+}
+
+static void* coop_fn(int solver, int hist, int pow2, int stage) {
     if (pow2) {
-        if (solver == 1) return hist == 0 ? (void*)k_window_coop<1, 0, 1> : (void*)k_window_coop<1, 1, 1>;
-        return hist == 0 ? (void*)k_window_coop<0, 0, 1> : (void*)k_window_coop<0, 1, 1>;
+        if (solver == 1) return hist == 0 ? coop_fn3<1, 0, 1>(stage) : coop_fn3<1, 1, 1>(stage);
+        return hist == 0 ? coop_fn3<0, 0, 1>(stage) : coop_fn3<0, 1, 1>(stage);
     }
-    if (solver == 1) return hist == 0 ? (void*)k_window_coop<1, 0, 0> : (void*)k_window_coop<1, 1, 0>;
-    return hist == 0 ? (void*)k_window_coop<0, 0, 0> : (void*)k_window_coop<0, 1, 0>;
+    if (solver == 1) return hist == 0 ? coop_fn3<1, 0, 0>(stage) : coop_fn3<1, 1, 0>(stage);
+    return hist == 0 ? coop_fn3<0, 0, 0>(stage) : coop_fn3<0, 1, 0>(stage);
 }
 
-cudaError_t window_prepare(const DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L) {
+cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L) {
     L->coop_block = block;
-    L->coop_smem = coop_smem_bytes(P.n_cells);
+    // staging when the block's shared memory stays within the per-block
+    // limit; then as many histogram copies (up to kHistCopiesMax) as fit
+    const size_t limit = 220 * 1024;
+    L->stage = coop_smem_bytes(P.n_cells, 1, block, 1) <= limit ? 1 : 0;
+    int copies = kHistCopiesMax;
+    while (copies > 1 && coop_smem_bytes(P.n_cells, copies, block, L->stage) > limit) copies >>= 1;
+    P.hist_copies = copies;
+    L->coop_smem = coop_smem_bytes(P.n_cells, copies, block, L->stage);
+    // positions one block deposits into one field per cycle
+    long long need_blocks = (P.n + block - 1) / block;
     int bps = 1 << 30;
-    for (int s = 0; s < 2; ++s)
-        for (int hh = 0; hh < 2; ++hh) {
-            void* fn = coop_fn(s, hh, P.xs_fma);
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->coop_smem);
-            if (e != cudaSuccess) return e;
-            int b = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, L->coop_smem);
-            if (e != cudaSuccess) return e;
-            bps = b < bps ? b : bps;
-        }
+    for (int hh = 0; hh < 2; ++hh) {
+        void* fn = coop_fn(P.solver, hh, P.xs_fma, L->stage);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->coop_smem);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, L->coop_smem);
+        if (e != cudaSuccess) return e;
+        bps = b < bps ? b : bps;
+    }
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const int want = blocks_per_sm > 0 ? blocks_per_sm : 1;
     if (want < bps) bps = want;
-    long long need = (P.n + block - 1) / block;
     long long grid = (long long)bps * sm_count;
-    if (need < grid) grid = need < 1 ? 1 : need;
+    if (need_blocks < grid) grid = need_blocks < 1 ? 1 : need_blocks;
     L->coop_grid = (int)grid;
-    // positions one block deposits into one field per cycle
     const long long per_thread = (P.n + grid * block - 1) / (grid * block);
     L->hist = per_thread * block <= 65536 ? 0 : 1;
+    if (L->hist == 1) P.hist_copies = 1;
     return cudaSuccess;
 }
 
 cudaError_t launch_window_coop(const DevParams& P, const WinBufs& B, const WindowLaunch& L, int mode,
                                int T_known, long long n_fine, cudaStream_t st, long long* launches,
                                const double* Tin) {
-    void* fn = coop_fn(P.solver, L.hist, P.xs_fma);
+    void* fn = coop_fn(P.solver, L.hist, P.xs_fma, L.stage);
     DevParams Pc = P;
     WinBufs Bc = B;
     void* args[] = {&Pc, &Bc, &mode, &T_known, &n_fine, &Tin};
