@@ -116,6 +116,7 @@ def _load():
             sig = {
                 "orc_derive": (i32, [P(Params), P(Derived)]),
                 "orc_deposit": (i32, [P(Params), i64, pd, pi64, pi64]),
+                "orc_deposit_f32": (i32, [P(Params), i64, P(C.c_float), pi64, pi64]),
                 "orc_poisson": (i32, [P(Params), i64, pi64, pi64, pd, pd]),
                 "orc_gather": (i32, [P(Params), i64, pd, pd, pd, pd]),
                 "orc_field": (i32, [P(Params), i64, pd, pd]),
@@ -168,6 +169,16 @@ def deposit(cfg: Config, R):
     Q = np.zeros(cfg.n_cells + 1, np.int64)
     n_out = np.zeros(1, np.int64)
     _check(_load().orc_deposit(C.byref(cfg.to_c()), R.size, _pd(R), _pi64(Q), _pi64(n_out)), "deposit")
+    return Q, int(n_out[0])
+
+
+def deposit_f32(cfg: Config, R):
+    """The CIC deposit with binary32 position arithmetic (the FP32 form's quantisation)."""
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    Q = np.zeros(cfg.n_cells + 1, np.int64)
+    n_out = np.zeros(1, np.int64)
+    _check(_load().orc_deposit_f32(C.byref(cfg.to_c()), R.size, R.ctypes.data_as(C.POINTER(C.c_float)), _pi64(Q),
+                                   _pi64(n_out)), "deposit_f32")
     return Q, int(n_out[0])
 
 

@@ -116,6 +116,27 @@ int orc_deposit(const orc_params* p, int64_t n, const double* R, int64_t* Q, int
     return 0;
 }
 
+int orc_deposit_f32(const orc_params* p, int64_t n, const float* R, int64_t* Q, int64_t* n_out) {
+    orc_derived d;
+    if (orc_derive(p, &d) || n < 0 || (n > 0 && !R) || !Q) return -1;
+    const int64_t W = (int64_t)p->weight_fixed;
+    const float r_min = (float)p->r_min, inv_hr = (float)d.inv_hr, Wf = (float)W;
+    for (int64_t j = 0; j <= p->n_cells; ++j) Q[j] = 0;
+    int64_t out = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float x = (R[i] - r_min) * inv_hr;
+        if (!(x >= 0.0f) || !(x < (float)p->n_cells)) { ++out; continue; }
+        float fl = floorf(x);
+        int64_t j = (int64_t)fl;
+        float f = x - fl;
+        int64_t qR = (int64_t)floorf(f * Wf);
+        Q[j] += W - qR;
+        Q[j + 1] += qR;
+    }
+    if (n_out) *n_out = out;
+    return 0;
+}
+
 int orc_poisson(const orc_params* p, int64_t n_particles, const int64_t* Q, int64_t* S_out,
                 double* E, double* rE_edges) {
     orc_derived d;

@@ -56,6 +56,11 @@ int  orc_derive(const orc_params* p, orc_derived* d);
 /* Mesh operations (Poisson model). */
 int  orc_deposit(const orc_params* p, int64_t n, const double* R,
                  int64_t* Q /* n_cells+1 */, int64_t* n_out);
+/* The same deposit with the position arithmetic in binary32: the fixed-point
+   split (cell, floor(f W)) is decided in the precision of the FP32 form of
+   the CUDA path, as an integer decision must be compared in the precision
+   it is taken in.  Positions are given as float. */
+int  orc_deposit_f32(const orc_params* p, int64_t n, const float* R, int64_t* Q, int64_t* n_out);
 int  orc_poisson(const orc_params* p, int64_t n_particles, const int64_t* Q,
                  int64_t* S /* n_cells+1, may be NULL */, double* E /* n_cells+1 */,
                  double* rE_edges /* 2 */);

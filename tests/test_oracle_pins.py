@@ -238,6 +238,26 @@ def test_deposit_partition_of_unity_and_first_moment():
     assert np.array_equal(Q, Q2)
 
 
+def test_deposit_f32_pins():
+    # binary32 deposit: partition of unity, first moment within one unit per
+    # particle, and equal to the FP64 deposit on dyadic positions (exact in
+    # both precisions)
+    c = pcfg()
+    W = c.weight_fixed
+    rng = np.random.default_rng(12)
+    R = np.concatenate([rng.normal(0, 1.5, 5000), [-4.0, 4.0, -4.5, 9.0]]).astype(np.float32)
+    Q, n_out = oracle.deposit_f32(c, R)
+    assert int(Q.sum()) + n_out * W == R.size * W
+    inside = (R >= -4.0) & (R < 4.0)
+    assert n_out == int((~inside).sum())
+    r = -4.0 + np.arange(257) * (8 / 256)
+    assert abs(float(np.dot(Q.astype(np.float64), r)) - W * float(R[inside].astype(np.float64).sum())) <= inside.sum() * (8 / 256) + 1e-6 * W * 5000
+    dy = (rng.integers(-4 * 1024, 4 * 1024, 3000) / 1024.0)
+    Qd, _ = oracle.deposit(c, dy)
+    Qf, _ = oracle.deposit_f32(c, dy.astype(np.float32))
+    assert np.array_equal(Qd, Qf)
+
+
 def test_deposit_brute_force_tiny():
     c = pcfg(n_cells=4, r_min=-1.0, r_max=1.0)  # nodes -1,-.5,0,.5,1
     W = c.weight_fixed
