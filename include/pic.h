@@ -22,8 +22,10 @@
  *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream).  Work is enqueued on it; calls that return data or a status
  *    synchronise that stream.
- *  - Particle state is FP64 structure-of-arrays: R[n], V[n] (the paper's
- *    y = (R, V)).  Periods are reported in units of time.
+ *  - Particle state crosses the boundary as FP64 arrays R[n], V[n] (the
+ *    paper's y = (R, V)), whatever the precision the handle computes in
+ *    (precision 1 rounds them to binary32 on the way in).  Periods are
+ *    reported in units of time, except in checkpoints (fine steps).
  *  - All computation runs in the library's CUDA kernels.  There is no CPU
  *    fallback: without a usable CUDA device, pic_init and the standalone
  *    mesh calls return PIC_ERR_CUDA.
@@ -77,7 +79,13 @@ typedef struct {
     int32_t  max_window_steps; /* fine steps a window may run; >= 2*spt + 2       */
     int32_t  periods_once;     /* 1: periods computed once at pic_init and kept
                                   (the Duffing case of Sec. 4.1); 0: every step  */
-    int32_t  precision;        /* 0 = FP64 (only value served)                    */
+    int32_t  precision;        /* 0 = FP64; 1 = FP32 form: particle state and push
+                                  in binary32 (Lawson RK4 in the rotating frame,
+                                  compensated integer+fraction times), FP64 only
+                                  in the charge -> field conversion and in
+                                  pic_moments; needs PIC_FINE_LAWSON_RK4, W <=
+                                  2^32 (Poisson) and dt/h < 2^22, else
+                                  PIC_ERR_UNSUPPORTED                            */
     int32_t  block_size;       /* CUDA threads per block, 0 = library default
                                   (1024 Poisson, 128 otherwise)                 */
     int32_t  blocks_per_sm;    /* Poisson window blocks per SM, 0 = default (1)   */
@@ -160,9 +168,10 @@ int pic_get_periods(pic_handle* h, double* T, int64_t* N, double* o, int ptr_kin
 int pic_get_field(pic_handle* h, int64_t* Q, double* E, double* rE_edges, int64_t* n_out,
                   int ptr_kind);
 
-/* Checkpoint: particle state, periods (time), time and step count.  The
-   arrays are caller-owned host memory of n_particles doubles each.  Resuming
-   from a checkpoint reproduces an uninterrupted run bit for bit. */
+/* Checkpoint: particle state, periods (in fine steps h, the library's own
+   unit), time and step count.  The arrays are caller-owned host memory of
+   n_particles doubles each.  Resuming from a checkpoint reproduces an
+   uninterrupted run bit for bit. */
 typedef struct {
     double* r;
     double* v;
@@ -200,6 +209,14 @@ int64_t pic_launch_count(const pic_handle* h);
 int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_dev,
                 int64_t* n_out_dev, void* stream);
 
+/* The same deposit with the quantisation of the FP32 form (precision 1):
+   x = (R - r_min) * (1/h_r), j = floor(x), f = x - j and floor(f*W) are all
+   evaluated in binary32 (r_min and 1/h_r rounded once to binary32), so the
+   integer charge of binary32 positions is defined without any FP64 step.
+   R_dev holds n binary32 positions; otherwise as pic_deposit. */
+int pic_deposit_f32(const pic_params* p, int64_t n, const float* R_dev, int64_t* Q_dev,
+                    int64_t* n_out_dev, void* stream);
+
 /* Trapezoid integral of d/dr(rE) = rho (eq. VlasPoissAxSymBeam, Sec. 2.3)
    from r = 0 outward: S_j = sum of (Q_m + Q_{m+1}) over the cells between
    node n_cells/2 and node j (negative on the left), computed as an exact
@@ -236,12 +253,13 @@ int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double
                const double* rE_edges_dev, double* e_dev, void* stream);
 
 /* ---- testing ------------------------------------------------------------ */
-/* Runs one macro step of a small Poisson beam whose grid barrier waits for
-   one more arrival than the grid has, so the wait can only end by its time
-   limit (wait_limit_ns, 1 ns..10 s).  Returns the status pic_step reports:
-   PIC_ERR_TIMEOUT when the limit works; the device stays usable.  Exercises
-   the failure path of every device-side wait without faulting the GPU. */
-int pic_test_barrier_timeout(int64_t wait_limit_ns, void* stream);
+/* Runs one macro step of a small Poisson beam (in the given precision, 0 or
+   1) whose grid barrier waits for one more arrival than the grid has, so
+   the wait can only end by its time limit (wait_limit_ns, 1 ns..10 s).
+   Returns the status pic_step reports: PIC_ERR_TIMEOUT when the limit
+   works; the device stays usable.  Exercises the failure path of every
+   device-side wait without faulting the GPU. */
+int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,7 @@ constexpr double kPi = 3.14159265358979323846;
 int map_cuda(cudaError_t e) {
     if (e == cudaSuccess) return PIC_OK;
     if (e == cudaErrorMemoryAllocation) return PIC_ERR_NO_MEMORY;
+    if (e == cudaErrorNotSupported) return PIC_ERR_UNSUPPORTED;
     return PIC_ERR_CUDA;
 }
 
@@ -39,7 +40,16 @@ int check_params(const pic_params* p, bool need_mesh) {
     if (p->steps_per_turn < 4 || p->steps_per_turn > (1 << 20)) return PIC_ERR_INVALID_ARG;
     if (p->max_window_steps < 2 * p->steps_per_turn + 2 || p->max_window_steps > (1 << 24))
         return PIC_ERR_INVALID_ARG;
-    if (p->precision != 0) return PIC_ERR_UNSUPPORTED;
+    if (p->precision != 0 && p->precision != 1) return PIC_ERR_INVALID_ARG;
+    if (p->precision == 1) {
+        // FP32 form: the exact-rotation solver (in the rotating frame), a
+        // fixed-point weight that binary32 weights split into 32-bit parts,
+        // and dt/h small enough for the compensated time arithmetic
+        if (p->fine_solver != PIC_FINE_LAWSON_RK4) return PIC_ERR_UNSUPPORTED;
+        if (p->field_model == PIC_FIELD_POISSON && p->weight_fixed > (1ull << 32)) return PIC_ERR_UNSUPPORTED;
+        const double D = p->dt / ((2.0 * kPi * p->eps) / (double)p->steps_per_turn);
+        if (!(D < 4194304.0)) return PIC_ERR_UNSUPPORTED;
+    }
     if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 1024 || (p->block_size & 31)))
         return PIC_ERR_INVALID_ARG;
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_ERR_INVALID_ARG;
@@ -105,6 +115,46 @@ void make_devparams(const pic_params* p, long long n, DevParams* d) {
     d->n = n;
     d->wait_ns = p->wait_limit_ns > 0 ? p->wait_limit_ns : 2000000000ll;
     d->bar_extra = 0;
+    // FP32 form: the same constants rounded once to binary32
+    d->r_min_f = (float)p->r_min;
+    d->inv_hr_f = (float)d->inv_hr;
+    d->ncells_f = (float)p->n_cells;
+    d->Wf = (float)p->weight_fixed;
+    d->h2shh_f = (float)(d->h2 * d->sh);
+    d->hshh_f = (float)(d->h * d->sh);
+    d->h6_f = (float)d->h6;
+    d->spt = p->steps_per_turn;
+    const double Dfl = std::floor(d->D);
+    d->Di = (int)Dfl;
+    d->Df = (float)(d->D - Dfl);
+    if (d->Df >= 1.0f) {
+        d->Di += 1;
+        d->Df = 0.0f;
+    }
+    d->rot = nullptr;
+}
+
+// Rotation table of the FP32 form: entry m = (cos, sin)(m pi / spt), the
+// exact E = 0 flow over m half fine steps, m = 0 .. 2 spt - 1, in FP64
+// rounded once to binary32.  Entries whose exact value is 0 or +-1 (quarter
+// turns) are stored exactly.
+std::vector<float2> rotation_table(int spt) {
+    std::vector<float2> t((size_t)2 * spt);
+    for (int m = 0; m < 2 * spt; ++m) {
+        float c, sn;
+        if ((2 * m) % spt == 0) {  // multiple of a quarter turn
+            const int q = (2 * m) / spt;  // 0..3
+            const float cq[4] = {1.0f, 0.0f, -1.0f, 0.0f}, sq[4] = {0.0f, 1.0f, 0.0f, -1.0f};
+            c = cq[q];
+            sn = sq[q];
+        } else {
+            const double x = kPi * (double)m / (double)spt;
+            c = (float)std::cos(x);
+            sn = (float)std::sin(x);
+        }
+        t[(size_t)m] = make_float2(c, sn);
+    }
+    return t;
 }
 
 int current_sm_count(int* sms) {
@@ -149,6 +199,13 @@ struct pic_handle {
     long long* part_i = nullptr;
     int mom_grid = 1;
     int* status_host = nullptr;  // pinned
+    // FP32 form (precision 1)
+    int prec = 0;
+    pic::WinBufs32 B32;
+    float2* y32_alt = nullptr;
+    pic::CTime *Tin32 = nullptr, *Tin32_alt = nullptr;
+    float2* rot32 = nullptr;
+    pic::SortBufs32 sort32;
     double t = 0.0;
     long long n_steps = 0;
     int have_periods = 0;
@@ -224,6 +281,7 @@ void collect_window_ms(pic_handle* h) {
 // Phase-space sort of the storage order before a window (see sort.cu).
 cudaError_t maybe_sort(pic_handle* h, long long step_index) {
     if (h->prm.sort_every <= 0 || step_index % h->prm.sort_every != 0) return cudaSuccess;
+    if (h->prec) return pic::launch_phase_sort32(h->sort32, h->n, h->sm_count, h->st, &h->launches);
     return pic::launch_phase_sort(h->sort, h->n, h->sm_count, h->st, &h->launches);
 }
 
@@ -240,9 +298,13 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
             if (e == cudaSuccess) e = reset_coop(h);
             const bool timed = e == cudaSuccess && ensure_events(h, h->ev_used + 2) == cudaSuccess;
             if (timed) cudaEventRecord(h->ev[h->ev_used], h->st);
-            if (e == cudaSuccess)
-                e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, mode == pic::MODE_FINE ? n_iter : 0,
-                                            h->st, &h->launches, h->Tin);
+            if (e == cudaSuccess) {
+                const long long nf = mode == pic::MODE_FINE ? n_iter : 0;
+                if (h->prec)
+                    e = pic::launch_window32_coop(h->dp, h->B32, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin32);
+                else
+                    e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin);
+            }
             if (timed) {
                 cudaEventRecord(h->ev[h->ev_used + 1], h->st);
                 h->ev_used += 2;
@@ -251,14 +313,148 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     } else {
         if (mode == pic::MODE_ETD) e = maybe_sort(h, 0);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
-        if (e == cudaSuccess)
-            e = pic::launch_window_local(h->dp, h->B, mode, T_known, mode == pic::MODE_PERIODS ? 0 : n_iter,
-                                         h->block, h->sm_count, h->st, &h->launches, h->Tin);
+        if (e == cudaSuccess) {
+            const long long ni = mode == pic::MODE_PERIODS ? 0 : n_iter;
+            if (h->prec)
+                e = pic::launch_window32_local(h->dp, h->B32, mode, T_known, ni, h->block, h->sm_count, h->st,
+                                               &h->launches, h->Tin32);
+            else
+                e = pic::launch_window_local(h->dp, h->B, mode, T_known, ni, h->block, h->sm_count, h->st,
+                                             &h->launches, h->Tin);
+        }
     }
     if (e != cudaSuccess) return map_cuda(e);
     const int rc = read_status(h);
     collect_window_ms(h);
     return rc;
+}
+
+
+// Public-order (R, V) of the state into device arrays, and back from
+// h->tmpR / h->tmpV (FP32 form: rounded to nearest binary32).
+cudaError_t unpack_state(pic_handle* h, double* r, double* v) {
+    if (h->prec) return pic::launch_unpack_perm32(h->B32.y, h->perm, h->n, r, v, h->sm_count, h->st, &h->launches);
+    return pic::launch_unpack_perm(h->B.y, h->perm, h->n, r, v, h->sm_count, h->st, &h->launches);
+}
+cudaError_t pack_state(pic_handle* h) {
+    if (h->prec)
+        return pic::launch_pack_perm32(h->tmpR, h->tmpV, h->perm, h->n, h->B32.y, h->sm_count, h->st, &h->launches);
+    return pic::launch_pack_perm(h->tmpR, h->tmpV, h->perm, h->n, h->B.y, h->sm_count, h->st, &h->launches);
+}
+
+// Allocation and initial state of the FP32 form (precision 1).  The
+// synchronisation words (Qring, barrier, status) live in h->B and are
+// shared with B32.
+int init32(pic_handle* h, const double* r0, const double* v0, int ptr_kind) {
+    const pic_params* p = &h->prm;
+    const long long n = h->n;
+    const size_t N = (size_t)n;
+    const size_t Np1 = (size_t)p->n_cells + 1;
+    const long long ld = pic::window32_row_stride(n);
+    const size_t LD = (size_t)(ld > 0 ? ld : 128);
+    const bool poisson = p->field_model == PIC_FIELD_POISSON;
+    const bool need_traj = poisson || !p->periods_once;
+    h->prec = 1;
+    pic::WinBufs32& B = h->B32;
+    std::memset(&B, 0, sizeof(B));
+    B.ld = (long long)LD;
+    int rc = PIC_OK;
+#define ALLOC(ptr, cnt)                         \
+    do {                                        \
+        if (!rc) rc = dalloc(h, &(ptr), (cnt)); \
+    } while (0)
+    ALLOC(B.y, LD);
+    ALLOC(B.tr, LD);
+    if (poisson) ALLOC(B.ce, LD);
+    ALLOC(B.t1, N);
+    ALLOC(B.T, N);
+    ALLOC(B.o, N);
+    ALLOC(B.N, N);
+    ALLOC(h->tmpR, N);
+    ALLOC(h->tmpV, N);
+    ALLOC(h->perm, N);
+    ALLOC(h->rot32, (size_t)2 * p->steps_per_turn);
+    if (p->sort_every > 0) {
+        ALLOC(h->perm_alt, N);
+        ALLOC(h->y32_alt, LD);
+        ALLOC(h->skey, N);
+        ALLOC(h->scount, pic::kSortBinsTotal);
+        if (p->periods_once) ALLOC(h->Tin32_alt, N);
+    }
+    if (poisson) {
+        ALLOC(h->B.Qring, 3 * 2 * Np1 * pic::kQPad);
+        ALLOC(h->Qf, Np1);
+        ALLOC(h->nout_f, 1);
+        ALLOC(h->Ef, Np1);
+        ALLOC(h->edges_f, 2);
+    }
+    if (need_traj) ALLOC(B.traj, (size_t)p->max_window_steps * LD);
+    if (p->periods_once) ALLOC(h->Tin32, N);
+    ALLOC(h->B.notdone, 3);
+    ALLOC(h->B.bar, 64);
+    ALLOC(h->B.status, 1);
+    ALLOC(h->B.K_out, 1);
+#undef ALLOC
+    if (rc) return rc;
+    B.Qring = h->B.Qring;
+    B.notdone = h->B.notdone;
+    B.bar = h->B.bar;
+    B.status = h->B.status;
+    B.K_out = h->B.K_out;
+    if (poisson) {
+        char* mem = nullptr;
+        rc = dalloc(h, &mem, pic::scan_scratch_bytes(p->n_cells));
+        if (rc) return rc;
+        const int tiles = (p->n_cells + pic::kScanTile - 1) / pic::kScanTile;
+        pic::scan_scratch_layout(p->n_cells, tiles, mem, &h->S);
+    }
+    {
+        long long want = (n + 255) / 256;
+        long long cap = (long long)h->sm_count * 4;
+        h->mom_grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+        rc = dalloc(h, &h->part_d, (size_t)h->mom_grid * pic::kMomDoubles);
+        if (!rc) rc = dalloc(h, &h->part_i, (size_t)h->mom_grid * pic::kMomInts);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaMallocHost(&h->status_host, sizeof(int));
+    if (e != cudaSuccess) return map_cuda(e);
+    const std::vector<float2> rot = rotation_table(p->steps_per_turn);
+    e = cudaMemcpyAsync(h->rot32, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice, h->st);
+    h->dp.rot = h->rot32;
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.y, 0, sizeof(float2) * LD, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B.tr, 0, sizeof(unsigned int) * LD, h->st);
+    if (e == cudaSuccess && h->y32_alt) e = cudaMemsetAsync(h->y32_alt, 0, sizeof(float2) * LD, h->st);
+    if (e == cudaSuccess && n > 0) {
+        e = cudaMemcpyAsync(h->tmpR, r0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v0, sizeof(double) * N, kind_to(ptr_kind), h->st);
+        if (e == cudaSuccess) e = pic::launch_iota(h->perm, n, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess) e = pic::launch_pack_perm32(h->tmpR, h->tmpV, h->perm, n, B.y, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.T, 0, sizeof(pic::CTime) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.o, 0, sizeof(pic::CTime) * N, h->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.N, 0, sizeof(int) * N, h->st);
+    }
+    if (e != cudaSuccess) return map_cuda(e);
+    pic::SortBufs32& S = h->sort32;
+    S.y = &h->B32.y;
+    S.y_alt = &h->y32_alt;
+    S.perm = &h->perm;
+    S.perm_alt = &h->perm_alt;
+    S.Tin = p->periods_once ? &h->Tin32 : nullptr;
+    S.Tin_alt = p->periods_once ? &h->Tin32_alt : nullptr;
+    S.key = h->skey;
+    S.count = h->scount;
+    if (poisson) {
+        rc = map_cuda(pic::window32_prepare(h->dp, h->block, p->blocks_per_sm, h->sm_count, B.ld, &h->L));
+        if (rc) return rc;
+    }
+    if (p->periods_once && n > 0) {
+        // step 1 once, at initialisation (Sec. 4.1)
+        rc = run_window(h, pic::MODE_PERIODS, 0);
+        if (!rc) rc = map_cuda(cudaMemcpyAsync(h->Tin32, B.T, sizeof(pic::CTime) * N, cudaMemcpyDeviceToDevice, h->st));
+        if (!rc) h->have_periods = 1;
+        if (rc) return rc;
+    }
+    return map_cuda(cudaStreamSynchronize(h->st));
 }
 
 }  // namespace
@@ -325,6 +521,17 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     h->sm_count = sms;
     make_devparams(p, n, &h->dp);
     h->block = p->block_size ? p->block_size : (p->field_model == PIC_FIELD_POISSON ? 1024 : 128);
+
+    if (p->precision == 1) {
+        rc = init32(h, r0, v0, ptr_kind);
+        if (rc) {
+            free_all(h);
+            delete h;
+            return rc;
+        }
+        *out = h;
+        return PIC_OK;
+    }
 
     const size_t N = (size_t)n;
     const size_t Np1 = (size_t)p->n_cells + 1;
@@ -460,8 +667,10 @@ int pic_get_field(pic_handle* h, int64_t* Q, double* E, double* rE_edges, int64_
     if (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE) return PIC_ERR_INVALID_ARG;
     if (h->n == 0) return PIC_ERR_INVALID_ARG;
     const size_t Np1 = (size_t)h->dp.n_cells + 1;
-    cudaError_t e = pic::launch_deposit(h->dp, (const double*)h->B.y, h->n, 2, h->Qf, h->nout_f, h->st, h->sm_count,
-                                        &h->launches);
+    cudaError_t e = h->prec ? pic::launch_deposit32(h->dp, (const float*)h->B32.y, h->n, 2, h->Qf, h->nout_f, h->st,
+                                                    h->sm_count, &h->launches)
+                            : pic::launch_deposit(h->dp, (const double*)h->B.y, h->n, 2, h->Qf, h->nout_f, h->st,
+                                                  h->sm_count, &h->launches);
     if (e == cudaSuccess) e = pic::launch_poisson(h->dp, h->Qf, h->Ef, h->edges_f, h->S, h->st, &h->launches);
     if (e == cudaSuccess && Q) e = cudaMemcpyAsync(Q, h->Qf, sizeof(long long) * Np1, kind_from(ptr_kind), h->st);
     if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, h->Ef, sizeof(double) * Np1, kind_from(ptr_kind), h->st);
@@ -485,7 +694,8 @@ int pic_moments(pic_handle* h, pic_moments_t* out) {
     std::vector<double> pd((size_t)G * pic::kMomDoubles);
     std::vector<long long> pi((size_t)G * pic::kMomInts);
     long long Kw = 0;
-    cudaError_t e = pic::launch_moments(h->dp, h->B, h->part_d, h->part_i, G, h->st, &h->launches);
+    cudaError_t e = h->prec ? pic::launch_moments32(h->dp, h->B32, h->part_d, h->part_i, G, h->st, &h->launches)
+                            : pic::launch_moments(h->dp, h->B, h->part_d, h->part_i, G, h->st, &h->launches);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pd.data(), h->part_d, sizeof(double) * pd.size(), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pi.data(), h->part_i, sizeof(long long) * pi.size(), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&Kw, h->B.K_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
@@ -542,10 +752,10 @@ int pic_get_particles(pic_handle* h, double* r, double* v, int ptr_kind) {
     if (h->n == 0) return PIC_OK;
     const size_t bytes = sizeof(double) * (size_t)h->n;
     cudaError_t e;
-    if (ptr_kind == PIC_PTR_DEVICE) {
-        e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, r, v, h->sm_count, h->st, &h->launches);
-    } else {
-        e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, h->tmpR, h->tmpV, h->sm_count, h->st, &h->launches);
+    double* dr = ptr_kind == PIC_PTR_DEVICE ? r : h->tmpR;
+    double* dv = ptr_kind == PIC_PTR_DEVICE ? v : h->tmpV;
+    e = unpack_state(h, dr, dv);
+    if (ptr_kind == PIC_PTR_HOST) {
         if (e == cudaSuccess && r) e = cudaMemcpyAsync(r, h->tmpR, bytes, cudaMemcpyDeviceToHost, h->st);
         if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, h->tmpV, bytes, cudaMemcpyDeviceToHost, h->st);
     }
@@ -560,7 +770,7 @@ int pic_set_particles(pic_handle* h, const double* r, const double* v, int ptr_k
     const size_t bytes = sizeof(double) * (size_t)h->n;
     cudaError_t e = cudaMemcpyAsync(h->tmpR, r, bytes, kind_to(ptr_kind), h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, v, bytes, kind_to(ptr_kind), h->st);
-    if (e == cudaSuccess) e = pic::launch_pack_perm(h->tmpR, h->tmpV, h->perm, h->n, h->B.y, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess) e = pack_state(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
 }
@@ -581,9 +791,15 @@ int pic_get_periods(pic_handle* h, double* T, int64_t* N, double* o, int ptr_kin
         dN = (long long*)((double*)tmp + 2 * n);
     }
     // per-slot results to the public order, in units of time
-    if (T) e = pic::launch_permute_d(h->B.T, h->perm, h->n, h->dp.h, 1, dT, h->sm_count, h->st, &h->launches);
-    if (e == cudaSuccess && o) e = pic::launch_permute_d(h->B.o, h->perm, h->n, h->dp.h, 1, dO, h->sm_count, h->st, &h->launches);
-    if (e == cudaSuccess && N) e = pic::launch_scatter_i(h->B.N, h->perm, h->n, dN, h->sm_count, h->st, &h->launches);
+    if (h->prec) {
+        if (T) e = pic::launch_ctime_out(h->B32.T, h->perm, h->n, h->dp.h, dT, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess && o) e = pic::launch_ctime_out(h->B32.o, h->perm, h->n, h->dp.h, dO, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess && N) e = pic::launch_scatter_i(h->B32.N, h->perm, h->n, dN, h->sm_count, h->st, &h->launches);
+    } else {
+        if (T) e = pic::launch_permute_d(h->B.T, h->perm, h->n, h->dp.h, 1, dT, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess && o) e = pic::launch_permute_d(h->B.o, h->perm, h->n, h->dp.h, 1, dO, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess && N) e = pic::launch_scatter_i(h->B.N, h->perm, h->n, dN, h->sm_count, h->st, &h->launches);
+    }
     if (ptr_kind == PIC_PTR_HOST) {
         if (e == cudaSuccess && T) e = cudaMemcpyAsync(T, dT, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
         if (e == cudaSuccess && o) e = cudaMemcpyAsync(o, dO, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -602,11 +818,18 @@ int pic_get_state(pic_handle* h, pic_state_t* out) {
     if (h->n == 0) return PIC_OK;
     if (!out->r || !out->v || !out->T) return PIC_ERR_INVALID_ARG;
     const size_t n = (size_t)h->n;
-    cudaError_t e = pic::launch_unpack_perm(h->B.y, h->perm, h->n, h->tmpR, h->tmpV, h->sm_count, h->st, &h->launches);
+    cudaError_t e = unpack_state(h, h->tmpR, h->tmpV);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->r, h->tmpR, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->v, h->tmpV, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
-    const double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
-    if (e == cudaSuccess) e = pic::launch_permute_d(Ts, h->perm, h->n, 1.0, 1, h->tmpR, h->sm_count, h->st, &h->launches);
+    if (e == cudaSuccess) {
+        if (h->prec) {
+            const pic::CTime* Ts = h->prm.periods_once ? h->Tin32 : h->B32.T;
+            e = pic::launch_ctime_out(Ts, h->perm, h->n, 1.0, h->tmpR, h->sm_count, h->st, &h->launches);
+        } else {
+            const double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
+            e = pic::launch_permute_d(Ts, h->perm, h->n, 1.0, 1, h->tmpR, h->sm_count, h->st, &h->launches);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out->T, h->tmpR, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     return map_cuda(e);
@@ -621,10 +844,17 @@ int pic_set_state(pic_handle* h, const pic_state_t* in) {
     if (n > 0) {
         e = cudaMemcpyAsync(h->tmpR, in->r, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpV, in->v, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
-        if (e == cudaSuccess) e = pic::launch_pack_perm(h->tmpR, h->tmpV, h->perm, h->n, h->B.y, h->sm_count, h->st, &h->launches);
-        double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
+        if (e == cudaSuccess) e = pack_state(h);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->tmpR, in->T, n * sizeof(double), cudaMemcpyHostToDevice, h->st);
-        if (e == cudaSuccess) e = pic::launch_permute_d(h->tmpR, h->perm, h->n, 1.0, 0, Ts, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess) {
+            if (h->prec) {
+                pic::CTime* Ts = h->prm.periods_once ? h->Tin32 : h->B32.T;
+                e = pic::launch_ctime_in(h->tmpR, h->perm, h->n, Ts, h->sm_count, h->st, &h->launches);
+            } else {
+                double* Ts = h->prm.periods_once ? h->Tin : h->B.T;
+                e = pic::launch_permute_d(h->tmpR, h->perm, h->n, 1.0, 0, Ts, h->sm_count, h->st, &h->launches);
+            }
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     }
     if (e != cudaSuccess) return map_cuda(e);
@@ -664,6 +894,19 @@ int pic_deposit(const pic_params* p, int64_t n, const double* R_dev, int64_t* Q_
     make_devparams(p, n, &d);
     return map_cuda(pic::launch_deposit(d, R_dev, n, 1, (long long*)Q_dev, (long long*)n_out_dev,
                                         (cudaStream_t)stream, sms, nullptr));
+}
+
+int pic_deposit_f32(const pic_params* p, int64_t n, const float* R_dev, int64_t* Q_dev, int64_t* n_out_dev,
+                    void* stream) {
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !R_dev) || !Q_dev || !n_out_dev) return PIC_ERR_INVALID_ARG;
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+    DevParams d;
+    make_devparams(p, n, &d);
+    return map_cuda(pic::launch_deposit32(d, R_dev, n, 1, (long long*)Q_dev, (long long*)n_out_dev,
+                                          (cudaStream_t)stream, sms, nullptr));
 }
 
 }  // extern "C"
@@ -724,11 +967,13 @@ int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double
 
 // Testing hook: a Poisson window whose grid barrier waits for one arrival
 // that never comes, with the given limit; returns the status pic_step gives.
-int pic_test_barrier_timeout(int64_t wait_limit_ns, void* stream) {
+int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* stream) {
     if (wait_limit_ns <= 0 || wait_limit_ns > 10000000000ll) return PIC_ERR_INVALID_ARG;
+    if (precision != 0 && precision != 1) return PIC_ERR_INVALID_ARG;
     pic_params p;
     pic_default_params(&p);
     p.wait_limit_ns = wait_limit_ns;
+    p.precision = precision;
     p.block_size = 128;
     std::vector<double> r(256), v(256);
     for (int i = 0; i < 256; ++i) {

@@ -48,6 +48,41 @@ __global__ void k_deposit(DevParams P, const double* __restrict__ R, long long n
     }
 }
 
+// The same deposit with the binary32 quantisation of the FP32 form:
+// x = (R - r_min)/h_r, j = floor(x), f = x - j and floor(f W) all in
+// binary32 (W a power of two, so f W is exact).
+__global__ void k_deposit32(DevParams P, const float* __restrict__ R, long long n, int r_stride,
+                            unsigned long long* __restrict__ Q, unsigned long long* __restrict__ n_out, int use_smem) {
+    extern __shared__ unsigned long long hist32[];
+    const int Np1 = P.n_cells + 1;
+    if (use_smem) {
+        for (int j = threadIdx.x; j < Np1; j += blockDim.x) hist32[j] = 0ull;
+        __syncthreads();
+    }
+    unsigned long long* H = use_smem ? hist32 : Q;
+    unsigned int out = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const Cell32 c = locate32(P, R[i * r_stride]);
+        if (c.j >= 0) {
+            const unsigned long long qR = __float2ull_rz(c.a * P.Wf);
+            atomicAdd(&H[c.j], (unsigned long long)P.W - qR);
+            if (qR) atomicAdd(&H[c.j + 1], qR);
+        } else {
+            ++out;
+        }
+    }
+    out = __reduce_add_sync(0xffffffffu, out);
+    if ((threadIdx.x & 31) == 0 && out) atomicAdd(n_out, (unsigned long long)out);
+    if (use_smem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < Np1; j += blockDim.x) {
+            const unsigned long long v = hist32[j];
+            if (v) atomicAdd(&Q[j], v);
+        }
+    }
+}
+
 // ------------------------------------------------- decoupled look-back scan
 
 __device__ __forceinline__ void st_release_s32(int* p, int v) {
@@ -255,6 +290,23 @@ cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, int
     int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
     fn<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, r_stride, (unsigned long long*)Q, (unsigned long long*)n_out,
                                                use_smem);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit32(const DevParams& P, const float* R, long long n, int r_stride, long long* Q,
+                             long long* n_out, cudaStream_t st, int sm_count, long long* launches) {
+    const int Np1 = P.n_cells + 1;
+    cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(long long) * (size_t)Np1, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_out, 0, sizeof(long long), st);
+    if (e != cudaSuccess || n == 0) return e;
+    size_t smem = sizeof(unsigned long long) * (size_t)Np1;
+    int use_smem = smem <= 96 * 1024;
+    if (use_smem && smem > 48 * 1024) cudaFuncSetAttribute(k_deposit32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long long want = (n + 255) / 256;
+    int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
+    k_deposit32<<<grid, 256, use_smem ? smem : 0, st>>>(P, R, n, r_stride, (unsigned long long*)Q,
+                                                        (unsigned long long*)n_out, use_smem);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

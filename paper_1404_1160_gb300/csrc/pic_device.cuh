@@ -45,6 +45,13 @@ struct DevParams {
     long long wait_ns;                 // limit of device-side waits
     int bar_extra;                     // testing only: arrivals a barrier waits for beyond the grid
     int hist_copies;                   // copies of each block's charge histogram (window kernel)
+    // FP32 form (precision 1): the same quantities rounded once to binary32
+    float r_min_f, inv_hr_f, ncells_f, Wf;
+    float h2shh_f, hshh_f, h6_f;       // (h/2) sin(h/(2 eps)), h sin(h/(2 eps)), h/6
+    int spt;                           // fine steps per turn of the E = 0 rotation
+    int Di;                            // dt/h = Di + Df with Df in [0, 1)
+    float Df;
+    const float2* rot;                 // 2 spt entries: (cos, sin)(m h / (2 eps))
 };
 
 // ---------------------------------------------------------------- mesh
@@ -370,6 +377,204 @@ __device__ __forceinline__ void lawson_step_analytic(const DevParams& P, int fie
     double e23 = e2 + e3;
     R = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), A);
     V = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, e4)), B);
+}
+
+// ============================================================ FP32 form
+//
+// Particle state and push in binary32.  Lawson RK4 is RK4 applied in the
+// frame that turns with the exact E = 0 flow: z = Phi(-t) y, where
+// Phi(s) = r(s/eps) is the rotation of eq. TRotationDef with T = 2 pi.  In
+// that frame the stiff linear part is gone and z changes only by the field
+// increments; the rotation of fine step k is read from a table of
+// (cos, sin)(m h/(2 eps)), m = 0 .. 2 spt - 1, computed once on the host in
+// FP64.  The table repeats exactly after one turn (spt fine steps), so no
+// phase is ever accumulated: each rotation carries one rounding, whatever
+// the step.  Times inside a window are kept as an integer number of fine
+// steps plus a binary32 fraction in [0, 1) (compensated time).
+
+// Index of the rotation of half-step m (m >= 0) in the table.
+__device__ __forceinline__ int rot_index(const DevParams& P, long long m) { return (int)(m % (2 * P.spt)); }
+
+// (Phi(t) z)_R and (Phi(t) z)_V for a table entry cs = (cos, sin)(t/eps).
+__device__ __forceinline__ float rot_R(float2 cs, float zR, float zV) { return fmaf(cs.x, zR, cs.y * zV); }
+__device__ __forceinline__ float rot_V(float2 cs, float zR, float zV) { return fmaf(cs.x, zV, -(cs.y * zR)); }
+
+// Stage positions of Lawson RK4 from z at fine step k, with a = Phi(t_k),
+// m = Phi(t_k + h/2), b = Phi(t_k + h) as table entries:
+//   R1 = (a z)_R, R3 = (m z)_R            (stage pair 1: no field needed)
+//   R2 = R3 + (h/2) sin(h/(2eps)) e1, R4 = (b z)_R + h sin(h/(2eps)) e3.
+__device__ __forceinline__ float lawson32_R2(const DevParams& P, float R3, float e1) { return fmaf(P.h2shh_f, e1, R3); }
+__device__ __forceinline__ float lawson32_R4(const DevParams& P, float2 b, float zR, float zV, float e3) {
+    return fmaf(P.hshh_f, e3, rot_R(b, zR, zV));
+}
+
+// z_{k+1} = z_k + h/6 [ e1 (-sin, cos)_a + 2 (e2 + e3) (-sin, cos)_m + e4 (-sin, cos)_b ]
+// (Phi(-t) applied to the field term (0, e) of each stage).
+__device__ __forceinline__ void lawson32_update(const DevParams& P, float2 a, float2 m, float2 b, float e1, float e2,
+                                                float e3, float e4, float& zR, float& zV) {
+    const float e23 = 2.0f * (e2 + e3);
+    const float dR = fmaf(e4, b.y, fmaf(e23, m.y, e1 * a.y));
+    const float dV = fmaf(e4, b.x, fmaf(e23, m.x, e1 * a.x));
+    zR = fmaf(-P.h6_f, dR, zR);
+    zV = fmaf(P.h6_f, dV, zV);
+}
+
+// A located binary32 position: cell j (or -1 below / -2 at or above the mesh
+// or NaN), right weight f (or R itself off the mesh) and qR = floor(f W).
+struct Cell32 {
+    int j;
+    float a;
+    unsigned int qR;
+};
+
+// x = (R - r_min) * (1/h_r) in binary32, j = floor(x), f = x - j (exact),
+// qR = floor(f W) (exact: W is a power of two <= 2^32).  Written without
+// branches: off the mesh (or NaN) the cell arithmetic runs on x = 0 and the
+// result is replaced.  NEED_Q: compute qR (deposits); the gathers need
+// only j and f.
+template <bool NEED_Q>
+__device__ __forceinline__ Cell32 locate32t(const DevParams& P, float R) {
+    const float x = (R - P.r_min_f) * P.inv_hr_f;
+    const bool in = x >= 0.0f && x < P.ncells_f;
+    const float xc = in ? x : 0.0f;
+    const float fl = floorf(xc);
+    const float f = xc - fl;
+    Cell32 c;
+    c.j = in ? (int)fl : (x < 0.0f ? -1 : -2);
+    c.a = in ? f : R;
+    c.qR = NEED_Q ? __float2uint_rz(f * P.Wf) : 0u;
+    return c;
+}
+__device__ __forceinline__ Cell32 locate32(const DevParams& P, float R) { return locate32t<true>(P, R); }
+
+// Field at a located position from a table of (E_j, E_{j+1} - E_j) per
+// cell; off the mesh rE keeps its edge value, E = rE_edge / R (binary32
+// fast division: the FP32 form's tolerance covers its 2 ulp).  Branch-free.
+__device__ __forceinline__ float gather32(const float2* tab, float rE_lo, float rE_hi, const Cell32& c) {
+    const float2 e = tab[c.j > 0 ? c.j : 0];
+    const float in = fmaf(c.a, e.y, e.x);
+    const float out = __fdividef(c.j == -1 ? rE_lo : rE_hi, c.a);
+    return c.j >= 0 ? in : out;
+}
+
+__device__ __forceinline__ float field_analytic32(int field, float R) { return field == 1 ? -((R * R) * R) : 0.0f; }
+
+__device__ __forceinline__ bool positive32(float v) { return __float_as_int(v) > 0; }
+
+__device__ __forceinline__ float interp3f(float y0, float y1, float y2, float s) {
+    const float d1 = ((-3.0f * y0 + 4.0f * y1) - y2) * 0.5f;
+    const float d2 = ((y0 - 2.0f * y1) + y2) * 0.5f;
+    return y0 + s * (d1 + s * d2);
+}
+
+// binary32 twin of quad_root01.
+__device__ __forceinline__ float quad_root01f(float v0, float v1, float v2) {
+    const float a = v0;
+    const float b = ((-3.0f * v0 + 4.0f * v1) - v2) * 0.5f;
+    const float c = ((v0 - 2.0f * v1) + v2) * 0.5f;
+    float s;
+    if (c == 0.0f) {
+        s = (b != 0.0f) ? -a / b : 0.0f;
+    } else {
+        float disc = b * b - 4.0f * a * c;
+        if (disc < 0.0f) disc = 0.0f;
+        const float sq = sqrtf(disc);
+        const float q = (b >= 0.0f) ? -0.5f * (b + sq) : -0.5f * (b - sq);
+        if (q == 0.0f) {
+            s = 0.0f;
+        } else {
+            s = a / q;
+            if (!(s >= 0.0f && s <= 1.0f)) s = q / c;
+        }
+    }
+    if (!(s >= 0.0f)) s = 0.0f;
+    if (s > 1.0f) s = 1.0f;
+    return s;
+}
+
+// A time (or period, remainder) in fine steps as i + f, i an integer and
+// f in [0, 1) a binary32 fraction.
+struct __align__(8) CTime {
+    int i;
+    float f;
+};
+
+__device__ __forceinline__ CTime ct_norm(long long i, float f) {
+    const float c = floorf(f);
+    i += (long long)c;
+    f -= c;
+    if (f >= 1.0f) {  // f - c rounded up to 1
+        f -= 1.0f;
+        ++i;
+    }
+    CTime t;
+    t.i = (int)i;
+    t.f = f;
+    return t;
+}
+__device__ __forceinline__ CTime ct_add(CTime a, CTime b) { return ct_norm((long long)a.i + b.i, a.f + b.f); }
+__device__ __forceinline__ CTime ct_sub(CTime a, CTime b) { return ct_norm((long long)a.i - b.i, a.f - b.f); }
+__device__ __forceinline__ bool ct_less(CTime a, CTime b) { return a.i < b.i || (a.i == b.i && a.f < b.f); }
+
+// Delta t = N T + o with o in [0, T) (eq. TimeStepDec) in compensated time:
+// N from the rounded quotient, then o = (Di - N Ti) + (Df - N Tf) with the
+// product N Tf split exactly (fma), and N corrected by at most a few steps.
+struct Decomp32 {
+    CTime T, o;
+    int N, need;
+};
+
+__device__ __forceinline__ Decomp32 decompose32(const DevParams& P, CTime T) {
+    Decomp32 d;
+    d.T = T;
+    const float Tt = (float)T.i + T.f, Dt = (float)P.Di + P.Df;
+    long long N = (long long)floorf(Dt / Tt);
+    if (N < 0) N = 0;
+    const float Nf = (float)N;
+    const float p = Nf * T.f;
+    const float pe = fmaf(Nf, T.f, -p);
+    CTime o = ct_norm((long long)P.Di - N * (long long)T.i, (P.Df - p) - pe);
+    for (int it = 0; it < 4 && o.i < 0; ++it) {
+        --N;
+        o = ct_add(o, T);
+    }
+    for (int it = 0; it < 4 && !ct_less(o, T); ++it) {
+        ++N;
+        o = ct_sub(o, T);
+    }
+    if (o.i < 0 || N < 0) {  // not reached for a validated T; keeps every sample index >= 0
+        o.i = 0;
+        o.f = 0.0f;
+        if (N < 0) N = 0;
+    }
+    d.o = o;
+    d.N = (int)N;
+    const CTime last = d.N > 0 ? ct_add(o, T) : o;
+    d.need = last.i + 2;
+    return d;
+}
+
+// Resolution of a particle's period in the FP32 form (the twin of
+// track_resolve): a non-positive period, or samples beyond the window cap,
+// take the fallback 2 pi eps (spt fine steps).
+__device__ __forceinline__ Decomp32 resolve32(const DevParams& P, CTime T, bool valid, int& flags) {
+    // valid: positive, finite, and Delta t / T small enough for the
+    // binary32 quotient to fix N to within the correction steps
+    const float Tt = (float)T.i + T.f;
+    if (!valid || T.i < 0 || !(Tt > 0.0f) || !isfinite(Tt) || !(((float)P.Di + P.Df) / Tt <= 4194304.0f)) {
+        flags |= F_FB;
+        T.i = P.spt;
+        T.f = 0.0f;
+    }
+    Decomp32 d = decompose32(P, T);
+    if (d.need > P.Kmax) {
+        flags |= F_FB;
+        T.i = P.spt;
+        T.f = 0.0f;
+        d = decompose32(P, T);
+    }
+    flags |= F_RES;
+    return d;
 }
 
 // ---------------------------------------------------------- device waits

@@ -85,6 +85,38 @@ cudaError_t launch_window_local(const DevParams& P, const WinBufs& B, int mode, 
                                 long long n_iter, int block, int sm_count, cudaStream_t st,
                                 long long* launches, const double* Tin);
 
+// FP32 form (window32.cu).  Rows of the trajectory have a stride of n
+// rounded up to a multiple of 128 slots (window32_row_stride); y, tr and
+// every row have that many slots, the ones past n being padding.
+struct WinBufs32 {
+    float2* y;                  // row 0: y^n in storage order
+    float2* traj;               // rows 1..Kmax: z_k, row k at traj + (k-1)*ld
+    unsigned int* tr;           // Track flags | need << 8
+    float2* ce;                 // (e1, e3) of the current step, from the second sweep to the first
+    CTime *t1, *T, *o;          // first extremum, period, remainder (fine steps)
+    int* N;                     // whole periods per macro step
+    unsigned long long* Qring;  // as WinBufs
+    int* notdone;
+    unsigned int* bar;
+    int* status;
+    long long* K_out;
+    long long ld;               // row stride (slots)
+};
+long long window32_row_stride(long long n);
+// Launch shape of the FP32 window; cudaErrorNotSupported when the mesh does
+// not fit in shared memory or a block would deposit more than 2^21
+// positions per field and cycle.
+cudaError_t window32_prepare(DevParams& P, int block, int blocks_per_sm, int sm_count, long long ld,
+                             WindowLaunch* L);
+cudaError_t launch_window32_coop(const DevParams& P, const WinBufs32& B, const WindowLaunch& L, int mode,
+                                 int T_known, long long n_fine, cudaStream_t st, long long* launches,
+                                 const CTime* Tin);
+cudaError_t launch_window32_local(const DevParams& P, const WinBufs32& B, int mode, int T_known, long long n_iter,
+                                  int block, int sm_count, cudaStream_t st, long long* launches, const CTime* Tin);
+// Binary32 deposit (the FP32 form's quantisation), R read as R[i * r_stride].
+cudaError_t launch_deposit32(const DevParams& P, const float* R, long long n, int r_stride, long long* Q,
+                             long long* n_out, cudaStream_t st, int sm_count, long long* launches);
+
 // Phase-space sort (sort.cu).  The pointers are swapped with their *_alt
 // buffers after each sort, so they are held by address.
 struct SortBufs {
@@ -110,12 +142,37 @@ cudaError_t launch_scatter_i(const int* src, const int* perm, long long n, long 
 cudaError_t launch_iota(int* perm, long long n, int sm_count, cudaStream_t st, long long* launches);
 constexpr int kSortBinsTotal = 1024 * 32;
 
+// The same for the FP32 form's storage.
+struct SortBufs32 {
+    float2** y;
+    float2** y_alt;
+    int** perm;
+    int** perm_alt;
+    CTime** Tin;
+    CTime** Tin_alt;
+    int* key;
+    unsigned int* count;
+};
+cudaError_t launch_phase_sort32(SortBufs32& S, long long n, int sm_count, cudaStream_t st, long long* launches);
+cudaError_t launch_unpack_perm32(const float2* y, const int* perm, long long n, double* R, double* V, int sm_count,
+                                 cudaStream_t st, long long* launches);
+cudaError_t launch_pack_perm32(const double* R, const double* V, const int* perm, long long n, float2* y,
+                               int sm_count, cudaStream_t st, long long* launches);
+// dst[perm[s]] = (src[s].i + src[s].f) * scale
+cudaError_t launch_ctime_out(const CTime* src, const int* perm, long long n, double scale, double* dst,
+                             int sm_count, cudaStream_t st, long long* launches);
+// dst[s] = split of src[perm[s]] into (floor, fraction)
+cudaError_t launch_ctime_in(const double* src, const int* perm, long long n, CTime* dst, int sm_count,
+                            cudaStream_t st, long long* launches);
+
 // Reductions for pic_moments: per-block partial sums, combined on the host
 // in a fixed order.
 constexpr int kMomDoubles = 8;   // sumR sumV sumR2 sumV2 sumR4 sumT minT maxT
 constexpr int kMomInts = 3;      // minN maxN n_fallback
 cudaError_t launch_moments(const DevParams& P, const WinBufs& B, double* part_d,
                            long long* part_i, int grid, cudaStream_t st, long long* launches);
+cudaError_t launch_moments32(const DevParams& P, const WinBufs32& B, double* part_d, long long* part_i, int grid,
+                             cudaStream_t st, long long* launches);
 
 }  // namespace pic
 

@@ -18,8 +18,7 @@ constexpr int kSortAmpBins = 32;
 constexpr int kSortBins = kSortAngleBins * kSortAmpBins;
 constexpr int kSortScanThreads = 1024;
 
-__device__ __forceinline__ int phase_key(double2 y) {
-    const float R = (float)y.x, V = (float)y.y;
+__device__ __forceinline__ int phase_key(float R, float V) {
     const float ang = atan2f(V, R);                          // (-pi, pi]
     int a = (int)((ang + 3.14159265f) * (kSortAngleBins / 6.28318531f));
     a = a < 0 ? 0 : (a >= kSortAngleBins ? kSortAngleBins - 1 : a);
@@ -29,12 +28,25 @@ __device__ __forceinline__ int phase_key(double2 y) {
     return a * kSortAmpBins + b;
 }
 
-__global__ void k_sort_keys(const double2* __restrict__ y, long long n, int* __restrict__ key,
+// Bin counts.  Particles that are already in key order share bins within a
+// warp, so the lanes of one bin add their count with a single atomic.  The
+// loop runs over whole warps (lanes past n carry no key).
+template <typename Y>
+__global__ void k_sort_keys(const Y* __restrict__ y, long long n, int* __restrict__ key,
                             unsigned int* __restrict__ count) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int k = phase_key(y[i]);
-        key[i] = k;
-        atomicAdd(&count[k], 1u);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+        const long long i = b + lane;
+        const bool valid = i < n;
+        int k = -1;
+        if (valid) {
+            const Y v = y[i];
+            k = phase_key((float)v.x, (float)v.y);
+            key[i] = k;
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)k);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&count[k], (unsigned int)__popc(peers));
     }
 }
 
@@ -77,13 +89,25 @@ __global__ void __launch_bounds__(kSortScanThreads) k_sort_scan(unsigned int* __
 }
 
 // Moves every particle (state, original index, and the kept periods) to
-// its slot in key order.
-__global__ void k_sort_scatter(const double2* __restrict__ y, const int* __restrict__ perm,
-                               const double* __restrict__ Tin, const int* __restrict__ key, long long n,
-                               unsigned int* __restrict__ cursor, double2* __restrict__ y_out,
-                               int* __restrict__ perm_out, double* __restrict__ Tin_out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned int d = atomicAdd(&cursor[key[i]], 1u);
+// its slot in key order; the lanes of a warp that share a bin take
+// consecutive slots from one atomic.
+template <typename Y, typename TT>
+__global__ void k_sort_scatter(const Y* __restrict__ y, const int* __restrict__ perm, const TT* __restrict__ Tin,
+                               const int* __restrict__ key, long long n, unsigned int* __restrict__ cursor,
+                               Y* __restrict__ y_out, int* __restrict__ perm_out, TT* __restrict__ Tin_out) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+        const long long i = b + lane;
+        const bool valid = i < n;
+        const int k = valid ? key[i] : -1;
+        const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)k);
+        const int leader = __ffs(peers) - 1;
+        unsigned int base = 0;
+        if (valid && lane == leader) base = atomicAdd(&cursor[k], (unsigned int)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (!valid) continue;
+        const unsigned int d = base + (unsigned int)__popc(peers & ((1u << lane) - 1u));
         y_out[d] = y[i];
         perm_out[d] = perm[i];
         if (Tin) Tin_out[d] = Tin[i];
@@ -148,9 +172,9 @@ cudaError_t launch_phase_sort(SortBufs& S, long long n, int sm_count, cudaStream
     cudaError_t e = cudaMemsetAsync(S.count, 0, sizeof(unsigned int) * kSortBins, st);
     if (e != cudaSuccess) return e;
     const int g = grid_of(n, sm_count);
-    k_sort_keys<<<g, 256, 0, st>>>(*S.y, n, S.key, S.count);
+    k_sort_keys<double2><<<g, 256, 0, st>>>(*S.y, n, S.key, S.count);
     k_sort_scan<<<1, kSortScanThreads, 0, st>>>(S.count);
-    k_sort_scatter<<<g, 256, 0, st>>>(*S.y, *S.perm, S.Tin ? *S.Tin : nullptr, S.key, n, S.count, *S.y_alt,
+    k_sort_scatter<double2, double><<<g, 256, 0, st>>>(*S.y, *S.perm, S.Tin ? *S.Tin : nullptr, S.key, n, S.count, *S.y_alt,
                                       *S.perm_alt, S.Tin ? *S.Tin_alt : nullptr);
     if (launches) *launches += 3;
     e = cudaGetLastError();
@@ -204,6 +228,114 @@ cudaError_t launch_scatter_i(const int* src, const int* perm, long long n, long 
 cudaError_t launch_iota(int* perm, long long n, int sm_count, cudaStream_t st, long long* launches) {
     if (n == 0) return cudaSuccess;
     k_iota<<<grid_of(n, sm_count), 256, 0, st>>>(perm, n);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP32 storage
+
+__global__ void k_unpack_perm32(const float2* __restrict__ y, const int* __restrict__ perm, long long n,
+                                double* __restrict__ R, double* __restrict__ V) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const float2 v = y[s];
+        const long long i = perm[s];
+        if (R) R[i] = (double)v.x;
+        if (V) V[i] = (double)v.y;
+    }
+}
+
+// y[s] = binary32 rounding (to nearest even) of (R, V)[perm[s]]
+__global__ void k_pack_perm32(const double* __restrict__ R, const double* __restrict__ V,
+                              const int* __restrict__ perm, long long n, float2* __restrict__ y) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const long long i = perm[s];
+        y[s] = make_float2(__double2float_rn(R[i]), __double2float_rn(V[i]));
+    }
+}
+
+__global__ void k_ctime_out(const CTime* __restrict__ src, const int* __restrict__ perm, long long n, double scale,
+                            double* __restrict__ dst) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const CTime t = src[s];
+        dst[perm[s]] = ((double)t.i + (double)t.f) * scale;
+    }
+}
+
+__global__ void k_ctime_in(const double* __restrict__ src, const int* __restrict__ perm, long long n,
+                           CTime* __restrict__ dst) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const double x = src[perm[s]];
+        CTime t;
+        if (x >= -2147483648.0 && x < 2147483647.0) {
+            const double fl = floor(x);
+            t.i = (int)fl;
+            t.f = __double2float_rn(x - fl);
+            if (t.f >= 1.0f) {
+                t.f = 0.0f;
+                ++t.i;
+            }
+        } else {
+            t.i = -1;  // not a usable period: the window takes the fallback
+            t.f = 0.0f;
+        }
+        dst[s] = t;
+    }
+}
+
+cudaError_t launch_phase_sort32(SortBufs32& S, long long n, int sm_count, cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(S.count, 0, sizeof(unsigned int) * kSortBins, st);
+    if (e != cudaSuccess) return e;
+    const int g = grid_of(n, sm_count);
+    k_sort_keys<float2><<<g, 256, 0, st>>>(*S.y, n, S.key, S.count);
+    k_sort_scan<<<1, kSortScanThreads, 0, st>>>(S.count);
+    k_sort_scatter<float2, CTime><<<g, 256, 0, st>>>(*S.y, *S.perm, S.Tin ? *S.Tin : nullptr, S.key, n, S.count,
+                                                      *S.y_alt, *S.perm_alt, S.Tin ? *S.Tin_alt : nullptr);
+    if (launches) *launches += 3;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    float2* ty = *S.y;
+    *S.y = *S.y_alt;
+    *S.y_alt = ty;
+    int* tp = *S.perm;
+    *S.perm = *S.perm_alt;
+    *S.perm_alt = tp;
+    if (S.Tin) {
+        CTime* tt = *S.Tin;
+        *S.Tin = *S.Tin_alt;
+        *S.Tin_alt = tt;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_unpack_perm32(const float2* y, const int* perm, long long n, double* R, double* V, int sm_count,
+                                 cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_unpack_perm32<<<grid_of(n, sm_count), 256, 0, st>>>(y, perm, n, R, V);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_perm32(const double* R, const double* V, const int* perm, long long n, float2* y,
+                               int sm_count, cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_pack_perm32<<<grid_of(n, sm_count), 256, 0, st>>>(R, V, perm, n, y);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctime_out(const CTime* src, const int* perm, long long n, double scale, double* dst,
+                             int sm_count, cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_ctime_out<<<grid_of(n, sm_count), 256, 0, st>>>(src, perm, n, scale, dst);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctime_in(const double* src, const int* perm, long long n, CTime* dst, int sm_count,
+                            cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_ctime_in<<<grid_of(n, sm_count), 256, 0, st>>>(src, perm, n, dst);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 //   shared-memory field table.
 // Histogram sets rotate over three buffers so one barrier per cycle suffices.
 #include "pic_internal.h"
+#include "window_common.cuh"
 
 namespace pic {
 
@@ -37,20 +38,15 @@ struct Hist {
 
 template <int HIST>
 __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cell& c, long long W) {
+    if (c.j < 0) return;
     if (HIST == 0) {
-        // lanes of a warp that share a cell add their counts and weight
-        // halves first (one set of shared atomics per distinct cell)
-        const unsigned int peers = __match_any_sync(0xffffffffu, (unsigned int)c.j);
+        // every lane adds its own position (plain shared atomics are faster
+        // on this GPU than merging the lanes of a warp first)
         const unsigned int lo = (unsigned int)(c.qR & 0xffff), hi = (unsigned int)(c.qR >> 16);
-        const unsigned int slo = __reduce_add_sync(peers, lo);
-        const unsigned int shi = __reduce_add_sync(peers, hi);
-        if (c.j >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-            atomicAdd(&h[c.j], (unsigned int)__popc(peers));
-            if (slo) atomicAdd(&h[Np1 + c.j], slo);
-            if (shi) atomicAdd(&h[2 * Np1 + c.j], shi);
-        }
+        atomicAdd(&h[c.j], 1u);
+        if (lo) atomicAdd(&h[Np1 + c.j], lo);
+        if (hi) atomicAdd(&h[2 * Np1 + c.j], hi);
     } else {
-        if (c.j < 0) return;
         unsigned long long* h64 = (unsigned long long*)h;
         atomicAdd(&h64[c.j], (unsigned long long)(W - c.qR));
         if (c.qR) atomicAdd(&h64[c.j + 1], (unsigned long long)c.qR);
@@ -78,59 +74,6 @@ __device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, i
     } else {
         return ((const unsigned long long*)h)[j];
     }
-}
-
-__device__ __forceinline__ long long warp_incl_scan64(long long x) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    return x;
-}
-
-// For both fields f = 0, 1: g_j = sum_{m<j} (q_m + q_{m+1}), j = 0..Nc
-// (block-wide exclusive scans in shared memory, done together).
-__device__ void block_exscan_pairs2(const long long* q, long long* g, int Nc, long long* s_warp) {
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
-    const int Np1 = Nc + 1;
-    const int per = (Nc + T - 1) / T;
-    const int beg = min(t * per, Nc), end = min(beg + per, Nc);
-    long long s0 = 0, s1 = 0;
-    for (int m = beg; m < end; ++m) {
-        s0 += q[m] + q[m + 1];
-        s1 += q[Np1 + m] + q[Np1 + m + 1];
-    }
-    const long long x0 = warp_incl_scan64(s0), x1 = warp_incl_scan64(s1);
-    if (lane == 31) {
-        s_warp[w] = x0;
-        s_warp[32 + w] = x1;
-    }
-    __syncthreads();
-    if (w == 0) {
-        long long y0 = (lane < nw) ? s_warp[lane] : 0, y1 = (lane < nw) ? s_warp[32 + lane] : 0;
-        y0 = warp_incl_scan64(y0);
-        y1 = warp_incl_scan64(y1);
-        if (lane < nw) {
-            s_warp[lane] = y0;
-            s_warp[32 + lane] = y1;
-        }
-    }
-    __syncthreads();
-    long long r0 = x0 - s0 + (w > 0 ? s_warp[w - 1] : 0);
-    long long r1 = x1 - s1 + (w > 0 ? s_warp[32 + w - 1] : 0);
-    for (int m = beg; m < end; ++m) {
-        g[m] = r0;
-        g[Np1 + m] = r1;
-        r0 += q[m] + q[m + 1];
-        r1 += q[Np1 + m] + q[Np1 + m + 1];
-    }
-    if (end == Nc && beg < end) {
-        g[Nc] = r0;
-        g[Np1 + Nc] = r1;
-    }
-    __syncthreads();
 }
 
 // Field tables of one cycle (two fields) from the cycle's global charge:
@@ -167,47 +110,6 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
         tab[idx].y = sl;
     }
     __syncthreads();
-}
-
-// Grid barrier with a time limit; false if any block timed out or failed.
-// Arrivals count on bar[0]; the last block of a generation publishes the
-// generation number in bar[32] (another cache line), which the others poll.
-__device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& gen,
-                                          int* status, int* s_ok) {
-    __syncthreads();
-    ++gen;
-    if (threadIdx.x == 0) {
-        const unsigned int target = gen * (gridDim.x + P.bar_extra);
-        __threadfence();
-        const unsigned int old = atomicAdd(bar, 1u);
-        int ok = 1;
-        if (old + 1 == target) {
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 32), "r"(gen) : "memory");
-        } else {
-            long long t0 = 0;
-            unsigned spins = 0;
-            while ((int)(ld_acquire_u32(bar + 32) - gen) < 0) {
-                if ((++spins & 31) == 0) {
-                    if (ld_acquire_s32(status) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    const long long now = global_ns();
-                    if (t0 == 0) {
-                        t0 = now;
-                    } else if (now - t0 > P.wait_ns) {
-                        atomicCAS(status, 0, (int)DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
 }
 
 // Period tracking of one particle at sample k (k >= 1), V_{k-1} = Vold,
@@ -274,26 +176,6 @@ __device__ __forceinline__ void flush_hist(const DevParams& P, const WinBufs& B,
         unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1 * kQPad;
         for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[(size_t)idx * kQPad] = 0ull;
     }
-}
-
-// ---- asynchronous staging of a warp's next chunk (cp.async, sm_80+)
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // One chunk (32 particles) of window state in shared memory; lane l owns
@@ -875,8 +757,10 @@ cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_co
     long long grid = (long long)bps * sm_count;
     if (need_blocks < grid) grid = need_blocks < 1 ? 1 : need_blocks;
     L->coop_grid = (int)grid;
+    // the split 32-bit histogram needs qR < 2^32 (W <= 2^32) and at most
+    // 65536 positions per block, field and cycle
     const long long per_thread = (P.n + grid * block - 1) / (grid * block);
-    L->hist = per_thread * block <= 65536 ? 0 : 1;
+    L->hist = (per_thread * block <= 65536 && P.W <= (1ll << 32)) ? 0 : 1;
     if (L->hist == 1) P.hist_copies = 1;
     return cudaSuccess;
 }

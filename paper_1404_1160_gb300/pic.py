@@ -132,10 +132,11 @@ def load() -> C.CDLL:
             "pic_destroy": (None, [H]),
             "pic_strerror": (C.c_char_p, [i32]),
             "pic_deposit": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
+            "pic_deposit_f32": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_poisson": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_poisson_noalloc": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
-            "pic_test_barrier_timeout": (i32, [i64, vp]),
+            "pic_test_barrier_timeout": (i32, [i64, i32, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -315,6 +316,12 @@ def pic_deposit(params: pic_params, R_dev, Q_dev, n_out_dev, stream=None) -> Non
     _check(load().pic_deposit(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(Q_dev)[0], _ptr(n_out_dev)[0], _stream(stream)), "pic_deposit")
 
 
+def pic_deposit_f32(params: pic_params, R_dev, Q_dev, n_out_dev, stream=None) -> None:
+    """Deposit of binary32 positions (torch.float32 device tensor) with the FP32 form's quantisation."""
+    _check(load().pic_deposit_f32(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(Q_dev)[0],
+                                  _ptr(n_out_dev)[0], _stream(stream)), "pic_deposit_f32")
+
+
 def pic_poisson(params: pic_params, n_particles: int, Q_dev, E_dev, edges_dev, stream=None) -> None:
     _check(load().pic_poisson(C.byref(params), n_particles, _ptr(Q_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _stream(stream)), "pic_poisson")
 
@@ -329,6 +336,6 @@ def pic_gather(params: pic_params, R_dev, E_dev, edges_dev, e_dev, stream=None) 
     _check(load().pic_gather(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _ptr(e_dev)[0], _stream(stream)), "pic_gather")
 
 
-def pic_test_barrier_timeout(wait_limit_ns: int, stream=None) -> int:
+def pic_test_barrier_timeout(wait_limit_ns: int, stream=None, precision: int = 0) -> int:
     """Returns the raw status (PIC_ERR_TIMEOUT expected)."""
-    return int(load().pic_test_barrier_timeout(wait_limit_ns, _stream(stream)))
+    return int(load().pic_test_barrier_timeout(wait_limit_ns, precision, _stream(stream)))

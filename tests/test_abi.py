@@ -82,10 +82,15 @@ def test_bad_arguments_rejected_without_device(lib):
     with pytest.raises(pic.PicError) as ei:
         pic.pic_init(p, np.zeros(4), np.zeros(4))
     assert ei.value.status == pic.PIC_ERR_INVALID_ARG
-    p = pic.pic_default_params(precision=1)
-    with pytest.raises(pic.PicError) as ei:
-        pic.pic_init(p, np.zeros(4), np.zeros(4))
-    assert ei.value.status == pic.PIC_ERR_UNSUPPORTED
+    # the FP32 form needs the exact-rotation solver and W <= 2^32; other
+    # precision values do not exist
+    for kw, rc in (({"precision": 1, "fine_solver": pic.PIC_FINE_RK4}, pic.PIC_ERR_UNSUPPORTED),
+                   ({"precision": 1, "weight_fixed": 1 << 33}, pic.PIC_ERR_UNSUPPORTED),
+                   ({"precision": 1, "dt": 1e5}, pic.PIC_ERR_UNSUPPORTED),
+                   ({"precision": 2}, pic.PIC_ERR_INVALID_ARG)):
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_init(pic.pic_default_params(**kw), np.zeros(4), np.zeros(4))
+        assert ei.value.status == rc
 
 
 def test_no_cpu_fallback_without_device(lib):

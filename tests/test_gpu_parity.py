@@ -149,6 +149,25 @@ def test_etd_step_poisson_matches_oracle(solver, n):
     pic.pic_destroy(h)
 
 
+@pytest.mark.parametrize("W_log2", [20, 40])
+def test_etd_step_with_other_fixed_point_weights(W_log2):
+    # W = 2^40: right weights floor(f W) above 2^32 (the 64-bit histogram);
+    # W = 2^20: a coarse quantisation of the same deposit
+    p = pic.pic_default_params(weight_fixed=1 << W_log2)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(20_001, seed=8, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 2)
+    R, V = pic.pic_get_particles(h)
+    Q, _, _, n_out = pic.pic_get_field(h, p.n_cells)
+    pic.pic_destroy(h)
+    res = oracle.etd_step(cfg, R0, V0)
+    res = oracle.etd_step(cfg, res.R, res.V)
+    Qo, no = oracle.deposit(cfg, res.R)
+    assert np.array_equal(Q, Qo) and n_out == no
+    assert bit_equal(R, res.R) and bit_equal(V, res.V)
+
+
 @pytest.mark.parametrize("solver", [pic.PIC_FINE_RK4, pic.PIC_FINE_LAWSON_RK4])
 def test_duffing_config0_shape_matches_oracle(solver):
     # Duffing, eps 0.01, dt 0.05 (N = 0), periods once at init (Sec. 4.1)
