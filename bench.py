@@ -9,7 +9,12 @@ for every particle (period detection, fine window with a full field cycle
 per stage, landing, extrapolation).  Metric: particle-steps/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload vp1e6|duffing1e4]
+                    [--workload vp1e6|duffing1e4|vp1e8_f32]
+
+`vp1e8_f32` is the FP32 form (precision 1): eps = 0.001, N_p = 1e8, 1024
+cells on [-4, 4], dt = 0.1; its line also carries the error of the FP32
+form against the FP64 path (itself bit-identical to the FP64 oracle) on a
+1e6-particle run of the same physics.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 (the only reference this method has) on a bounded sample of the same
@@ -43,6 +48,11 @@ WORKLOADS = {
     # Duffing test field, periods once at init
     "duffing1e4": dict(n=10**4, params=dict(field_model=1, dt=0.05, periods_once=1), r_cut=None,
                        desc="Duffing E=-r^3, eps=0.01, N_p=1e4, dt=0.05, periods once, FP64"),
+    # FP32 form of the same physics at eps = 1e-3 (N about 15 periods per step)
+    "vp1e8_f32": dict(n=10**8, params=dict(precision=1, eps=1e-3, n_cells=1024, max_window_steps=202, sort_every=4),
+                      r_cut=4.0, error_n=10**6, error_steps=20,
+                      desc="Vlasov-Poisson FP32 form, eps=0.001, N_p=1e8, N_r=1024 on [-4,4], CIC, dt=0.1, Lawson RK4 "
+                           "in the rotating frame, binary32 state, FP64 field conversion and diagnostics"),
 }
 
 # Algorithmic FP64 flops per particle per fine step of the Lawson RK4 window
@@ -51,15 +61,28 @@ WORKLOADS = {
 FLOPS_PER_PARTICLE_FINE_STEP = 56
 
 
-PROFILE = os.path.join(ROOT, "profiles", "window_coop_vp1e6.md")
-KERNEL_SOURCES = ["paper_1404_1160_gb300/csrc/window.cu", "paper_1404_1160_gb300/csrc/pic_device.cuh"]
+# FP32 form: the window streams its state; the least a streaming window
+# moves is the rotating-frame state of every particle in and out once per
+# fine step (8 B + 8 B).
+BYTES_PER_PARTICLE_FINE_STEP_F32 = 16
+
+# committed ncu summaries (DRAM traffic of the window kernel) and the sources
+# they were taken from
+PROFILES = {
+    "vp1e6": ("window_coop_vp1e6.md", ["paper_1404_1160_gb300/csrc/window.cu",
+                                       "paper_1404_1160_gb300/csrc/window_common.cuh",
+                                       "paper_1404_1160_gb300/csrc/pic_device.cuh"]),
+    "vp1e8_f32": ("window32_coop_vp1e8_f32.md", ["paper_1404_1160_gb300/csrc/window32.cu",
+                                                 "paper_1404_1160_gb300/csrc/window_common.cuh",
+                                                 "paper_1404_1160_gb300/csrc/pic_device.cuh"]),
+}
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(workload: str) -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in PROFILES[workload][1]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -68,7 +91,10 @@ def kernel_sources_sha256() -> str:
 def kernel_traffic(n: int, workload: str):
     """DRAM bytes per window launch from the committed ncu summary, or None
     when the kernel sources changed since it was captured (or no summary)."""
-    if workload != "vp1e6" or n != WORKLOADS["vp1e6"]["n"] or not os.path.exists(PROFILE):
+    if workload not in PROFILES or n != WORKLOADS[workload]["n"]:
+        return None
+    PROFILE = os.path.join(ROOT, "profiles", PROFILES[workload][0])
+    if not os.path.exists(PROFILE):
         return None
     sha = bytes_ = None
     for line in open(PROFILE):
@@ -76,7 +102,7 @@ def kernel_traffic(n: int, workload: str):
             sha = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_launch:"):
             bytes_ = float(line.split(":", 1)[1].strip())
-    if sha != kernel_sources_sha256() or bytes_ is None:
+    if sha != kernel_sources_sha256(workload) or bytes_ is None:
         return None
     return bytes_
 
@@ -215,7 +241,18 @@ def run_ours(args):
     mean_ms = float(np.mean(step_ms))
     K = mom["window_steps"]
     roofline = None
-    if prm.field_model == 0 and kernel_ms:
+    f32 = prm.precision == 1
+    if f32 and prm.field_model == 0 and kernel_ms:
+        kern_ms = float(np.mean(kernel_ms))
+        bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * n * K
+        achieved = bytes_ / (kern_ms / 1e3)
+        peak = measured_hbm_peak()
+        roofline = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": kernel_traffic(n, args.workload),
+                    "kernel": "k_window32_coop (FP32 form, one launch per macro step)",
+                    "kernel_ms": kern_ms, "fine_steps_per_launch": K, "algorithmic_bytes_per_launch": bytes_,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
+    elif prm.field_model == 0 and kernel_ms:
         kern_ms = float(np.mean(kernel_ms))
         flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
         achieved = flops / (kern_ms / 1e3)
@@ -227,7 +264,8 @@ def run_ours(args):
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if f32 else "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "n_particles": n, "fine_steps_per_window": K,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -237,13 +275,62 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clk.summary(),
-        "error_vs_oracle": "bit-identical R, V and charge on the parity tests (tolerance 1e-12 rel)",
+        "error_vs_oracle": ("FP32 form: see error_vs_fp64 (binary32 bounds checked against the FP64 oracle in the "
+                            "parity tests)") if f32 else
+                           "bit-identical R, V and charge on the parity tests (tolerance 1e-12 rel)",
     }
+    if f32 and "error_n" in wl:
+        line["error_vs_fp64"] = error_vs_fp64(args.workload)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def measured_hbm_peak() -> float:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        return float(json.load(fh)["hbm_gbs"]) * 1e9
+
+
+def error_vs_fp64(workload: str):
+    """Runs the same seeded beam through the FP32 form and the FP64 path
+    (bit-identical to the FP64 oracle) for a number of macro steps and
+    compares positions, velocities, energy and charge density."""
+    import torch
+
+    from paper_1404_1160_gb300 import inputs
+    from paper_1404_1160_gb300 import pic
+
+    wl = WORKLOADS[workload]
+    n, steps = wl["error_n"], wl["error_steps"]
+    R0, V0 = inputs.gaussian_beam(n, seed=0, r_cut=wl["r_cut"])
+    # both start from the same binary32-representable state
+    R0 = R0.astype(np.float32).astype(np.float64)
+    V0 = V0.astype(np.float32).astype(np.float64)
+    out = {}
+    for prec in (1, 0):
+        prm = pic.pic_default_params(**dict(wl["params"], precision=prec))
+        h = pic.pic_init(prm, R0, V0)
+        m0 = pic.pic_moments(h)
+        pic.pic_step(h, steps)
+        R, V = pic.pic_get_particles(h)
+        Q, _, _, n_out = pic.pic_get_field(h, prm.n_cells)
+        m1 = pic.pic_moments(h)
+        pic.pic_destroy(h)
+        out[prec] = (R, V, Q, m0, m1)
+    R32, V32, Q32, a0, a1 = out[1]
+    R64, V64, Q64, b0, b1 = out[0]
+    dR, dV = np.abs(R32 - R64), np.abs(V32 - V64)
+    torch.cuda.synchronize()
+    return {"n_particles": n, "macro_steps": steps, "max_abs_dR": float(dR.max()), "max_abs_dV": float(dV.max()),
+            "rms_dR": float(np.sqrt(np.mean(dR * dR))), "rms_dV": float(np.sqrt(np.mean(dV * dV))),
+            "kinetic_rel_diff": abs(a1["kinetic"] - b1["kinetic"]) / b1["kinetic"],
+            "kinetic_drift_f32": (a1["kinetic"] - a0["kinetic"]) / a0["kinetic"],
+            "kinetic_drift_f64": (b1["kinetic"] - b0["kinetic"]) / b0["kinetic"],
+            "density_L1_rel": float(np.abs(Q32 - Q64).sum() / np.abs(Q64).sum()),
+            "charge_exact_f32": bool(a1["Q_total"] + a1["n_out_of_mesh"] * (1 << 32) == n * (1 << 32)),
+            "reference": "FP64 path of this library (bit-identical to the FP64 oracle)"}
 
 
 def cpu_baseline(workload: str, n_sample: int):
@@ -282,7 +369,8 @@ def oracle_cfg(workload):
     p = dict(eps=0.01, dt=0.1, field_model=0, fine_solver=1, steps_per_turn=100, n_cells=256, r_min=-4.0, r_max=4.0,
              total_charge=1.0, weight_fixed=1 << 32, max_window_steps=300)
     q = dict(WORKLOADS[workload]["params"])
-    q.pop("periods_once", None)
+    for k in ("periods_once", "precision", "sort_every"):
+        q.pop(k, None)
     p.update(q)
     return oracle.Config(**p)
 
