@@ -83,3 +83,25 @@ def paper_beam(n: int = 20000, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
     r = PAPER_R_HALF_WIDTH * (2.0 * uniform(2 * seed + 1, 0, n) - 1.0)
     v = PAPER_V_TH * normal(2 * seed + 2, 0, n)
     return r, v
+
+
+# ---------------------------------------------------------------- learned stepper
+
+MLP_SHAPES = [("W1", (64, 5)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (2, 64)), ("b3", (2,))]
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Seeded Glorot-uniform starting weights of the learned stepper's network
+    (biases zero), flat float32 in the library's layout: W1 (64 x 5) | b1 |
+    W2 (64 x 64) | b2 | W3 (2 x 64) | b3."""
+    parts = []
+    start = 0
+    for name, shape in MLP_SHAPES:
+        n = int(np.prod(shape))
+        if name.startswith("W"):
+            a = np.sqrt(6.0 / (shape[0] + shape[1]))
+            parts.append((2.0 * uniform(seed, start, n) - 1.0) * a)
+        else:
+            parts.append(np.zeros(n))
+        start += n
+    return np.concatenate(parts).astype(np.float32)

@@ -443,3 +443,92 @@ def test_vlasov_poisson_step_tracks_brute_force():
         # charge is conserved exactly by the deposit
         Q, n_out = oracle.deposit(c, res.R)
         assert int(Q.sum()) + n_out * c.weight_fixed == 128 * c.weight_fixed
+
+
+# ------------------------------------------------------ learned-stepper network
+
+
+def test_mlp_bf16_rounding_matches_float32_bit_rounding():
+    # independent route: round float32 bit patterns to 16 bits, ties to even
+    from oracle import mlp
+
+    rng = np.random.default_rng(3)
+    x = (rng.normal(0, 3, 20000) * np.exp(rng.normal(0, 4, 20000))).astype(np.float32)
+    x = np.concatenate([x, np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-8, -2.5, 0.0], np.float32)])
+    b = x.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    ref = b.astype(np.uint32).view(np.float32).astype(np.float64)
+    assert np.array_equal(mlp.bf16(x.astype(np.float64)), ref)
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: even mantissa wins
+    assert mlp.bf16(np.array([1.0 + 2**-8]))[0] == 1.0
+
+
+def test_mlp_gelu_is_x_times_normal_cdf():
+    from scipy.special import ndtr
+
+    from oracle import mlp
+
+    u = np.linspace(-8, 8, 1001)
+    assert np.allclose(mlp.gelu(u), u * ndtr(u), rtol=5e-14, atol=1e-300)
+    h = 1e-6
+    fd = (mlp.gelu(u + h) - mlp.gelu(u - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_prime(u), fd, rtol=1e-7, atol=3e-9)
+
+
+def test_mlp_forward_matches_torch_cpu_layers():
+    # exact FP64 network against torch's own Linear and GELU (erf form)
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+
+    rng = np.random.default_rng(4)
+    w = rng.normal(0, 0.3, mlp.N_PARAMS)
+    X = rng.normal(0, 1, (37, 5))
+    p = mlp.unflatten(w)
+    net = torch.nn.Sequential(torch.nn.Linear(5, 64), torch.nn.GELU(), torch.nn.Linear(64, 64), torch.nn.GELU(),
+                              torch.nn.Linear(64, 2)).double()
+    with torch.no_grad():
+        for layer, (Wn, bn) in zip((net[0], net[2], net[4]), (("W1", "b1"), ("W2", "b2"), ("W3", "b3"))):
+            layer.weight.copy_(torch.from_numpy(p[Wn]))
+            layer.bias.copy_(torch.from_numpy(p[bn]))
+        ref = net(torch.from_numpy(X)).numpy()
+    assert np.allclose(mlp.forward(w, X, emulate_bf16=False)["out"], ref, rtol=1e-13, atol=1e-13)
+
+
+def test_mlp_gradients_match_finite_differences():
+    # backward of the exact FP64 network against central differences of its loss
+    from oracle import mlp
+
+    rng = np.random.default_rng(5)
+    w = rng.normal(0, 0.4, mlp.N_PARAMS)
+    X = rng.normal(0, 1, (23, 5))
+    Y = rng.normal(0, 1, (23, 2))
+    loss, g = mlp.loss_and_grads(w, X, Y, emulate_bf16=False)
+    idx = np.concatenate([rng.choice(mlp.N_PARAMS, 60, replace=False), [0, 319, 320, 383, 384, 4479, 4480, 4543, 4544,
+                                                                        4671, 4672, 4673]])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(w)
+        e[i] = h
+        fd = (mlp.loss_and_grads(w + e, X, Y, False)[0] - mlp.loss_and_grads(w - e, X, Y, False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fd, g[i])
+    assert loss > 0
+
+
+def test_mlp_bf16_rounding_points():
+    # with emulation on, the loss is that of the FP64 network evaluated on
+    # bfloat16 weights and bfloat16 hidden activations: rounding the weights
+    # beforehand changes nothing, and a weight set already in bfloat16 with
+    # activations that are exact in bfloat16 gives the exact network's loss
+    from oracle import mlp
+
+    rng = np.random.default_rng(6)
+    w = rng.normal(0, 0.3, mlp.N_PARAMS)
+    X = rng.normal(0, 1, (11, 5))
+    Y = rng.normal(0, 1, (11, 2))
+    p = mlp.unflatten(w)
+    for k in ("W1", "W2", "W3"):
+        p[k] = mlp.bf16(p[k])
+    wb = mlp.flatten(p)
+    assert mlp.loss_and_grads(w, X, Y, True)[0] == mlp.loss_and_grads(wb, X, Y, True)[0]
+    a = mlp.forward(w, X, True)
+    assert np.array_equal(a["h1b"], mlp.bf16(a["h1b"])) and np.array_equal(a["h2b"], mlp.bf16(a["h2b"]))
