@@ -252,6 +252,46 @@ int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, const int64_t*
 int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double* E_dev,
                const double* rE_edges_dev, double* e_dev, void* stream);
 
+/* ---- learned stepper ----------------------------------------------------- */
+/* The paper has no learned component: this network is an addition that
+   corrects one improved-ETD macro step (Algorithm ETDFSSModAlgo) taken with a
+   large Delta t.  It is a 5-64-64-2 perceptron,
+       x = (r, v, sin(t/eps), cos(t/eps), dt),
+       z1 = W1 x + b1, h1 = gelu(z1), z2 = W2 bf16(h1) + b2, h2 = gelu(z2),
+       out = W3 bf16(h2) + b3 = (dR, dV) correction,
+   gelu(u) = u erfc(-u/sqrt 2)/2, with W1..W3 the bfloat16 roundings of FP32
+   master weights and FP32 accumulation; the hidden layer and its backward run
+   on the tensor cores.  Parameters travel as PIC_MLP_PARAMS floats in the
+   order W1 (64x5, row-major) | b1 (64) | W2 (64x64) | b2 (64) | W3 (2x64) |
+   b3 (2).  Inputs X are n x 5 row-major floats, targets/outputs n x 2. */
+#define PIC_MLP_PARAMS 4674
+typedef struct pic_mlp pic_mlp;        /* opaque; owns its device memory */
+typedef struct {
+    float lr, beta1, beta2, eps;       /* Adam on the FP32 master weights */
+} pic_adam_t;
+
+int pic_mlp_num_params(void);
+/* Creates a network with all weights zero, able to train on batches of up to
+   max_batch samples (scratch of ~800 B per sample).  Work runs on stream. */
+int pic_mlp_create(int64_t max_batch, void* stream, pic_mlp** out);
+/* Copies PIC_MLP_PARAMS master weights in (and resets the Adam state) or out. */
+int pic_mlp_set_weights(pic_mlp* m, const float* w, int ptr_kind);
+int pic_mlp_get_weights(pic_mlp* m, float* w, int ptr_kind);
+/* out = network(X) for n samples (device pointers).  Synchronises. */
+int pic_mlp_forward(pic_mlp* m, int64_t n, const float* X_dev, float* Y_dev);
+/* Gradient of the loss sum((out - T)^2)/(2n) over n <= max_batch samples
+   (device X, T) and the loss itself, without updating the weights; grad
+   holds PIC_MLP_PARAMS floats, loss one (host or device per ptr_kind).
+   Reductions run in a fixed order: the result is reproducible bit for bit. */
+int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_dev, float* grad, float* loss,
+                      int ptr_kind);
+/* steps Adam steps on batches of `batch` samples drawn from n_data samples
+   (device X, T) along a fixed permutation chosen by seed; loss_hist (host,
+   `steps` floats, may be NULL) receives each batch loss.  Synchronises. */
+int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T_dev, int64_t batch, int64_t steps,
+                  const pic_adam_t* opt, uint64_t seed, float* loss_hist);
+void pic_mlp_destroy(pic_mlp* m);
+
 /* ---- testing ------------------------------------------------------------ */
 /* Runs one macro step of a small Poisson beam (in the given precision, 0 or
    1) whose grid barrier waits for one more arrival than the grid has, so

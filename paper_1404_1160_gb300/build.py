@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
-SOURCES = ["api.cu", "mesh.cu", "window.cu", "window32.cu", "sort.cu"]
+SOURCES = ["api.cu", "mesh.cu", "window.cu", "window32.cu", "sort.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

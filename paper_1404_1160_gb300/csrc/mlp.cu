@@ -1,0 +1,658 @@
+// mlp.cu -- the network of the learned stepper: a 5-64-64-2 GELU perceptron
+// with bfloat16 weights and FP32 accumulation, inference and training on the
+// tensor cores (mma.sync m16n8k16, bf16 x bf16 -> f32).  The paper has no
+// learned component; the network corrects one macro step of the improved ETD
+// scheme (Algorithm ETDFSSModAlgo) and is defined, with its rounding points,
+// as:
+//
+//   x = (r, v, sin(t/eps), cos(t/eps), dt)
+//   z1 = W1 x + b1,   h1 = gelu(z1)                 (CUDA cores, FP32)
+//   z2 = W2 bf16(h1) + b2,  h2 = gelu(z2)           (tensor cores)
+//   out = W3 bf16(h2) + b3                          (CUDA cores, FP32)
+//
+// W1, W2, W3 are the bfloat16 roundings of FP32 master weights; gelu(u) =
+// u erfc(-u / sqrt 2) / 2.  Training minimises sum((out - y)^2) / (2B) with
+// Adam on the master weights.  Backward:
+//   dout = (out - y) / B, dW3 = dout^T bf16(h2), db3 = sum dout,
+//   dz2 = (dout W3) gelu'(z2), dW2 = bf16(dz2)^T bf16(h1), db2 = sum dz2,
+//   dz1 = (bf16(dz2) W2) gelu'(z1), dW1 = dz1^T x, db1 = sum dz1.
+// The per-sample part (forward, dz1, dz2) runs one warp per 16 samples; the
+// weight gradients are reduced over the batch by a second kernel (dW2 on the
+// tensor cores) into per-block partials, which a third kernel sums in a fixed
+// order before the Adam update, so training is reproducible bit for bit.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+// flat parameter layout (FP32 masters)
+constexpr int kMIn = 5, kMHid = 64, kMOut = 2;
+constexpr int oW1 = 0, ob1 = oW1 + kMHid * kMIn, oW2 = ob1 + kMHid, ob2 = oW2 + kMHid * kMHid, oW3 = ob2 + kMHid,
+              ob3 = oW3 + kMOut * kMHid, kMParams = ob3 + kMOut;
+static_assert(kMParams == 4674, "parameter count");
+// compact FP32 block used by the CUDA-core layers: bf16-rounded W1 and W3, biases
+constexpr int sW1 = 0, sb1 = sW1 + kMHid * kMIn, sb2 = sb1 + kMHid, sW3 = sb2 + kMHid, sb3 = sW3 + kMOut * kMHid,
+              kMSmall = sb3 + kMOut;
+
+constexpr int kFbThreads = 128;  // 4 warps, 16 samples each per tile
+constexpr int kWgThreads = 128;  // weight-gradient blocks
+constexpr int kWgTile = 64;      // samples per staged tile
+constexpr int kWgMaxBlocks = 256;
+
+struct MlpDev {
+    float *master, *m, *v;
+    __nv_bfloat16* W2b;   // [j][k]
+    __nv_bfloat16* W2Tb;  // [k][j]
+    float* small;         // kMSmall
+    // training scratch for up to max_batch samples
+    float* xs;            // [B][5]
+    float* dz1;           // [B][64]
+    float* dz2;           // [B][64]
+    __nv_bfloat16* h1b;   // [B][64]
+    __nv_bfloat16* h2b;   // [B][64]
+    float* dout;          // [B][2]
+    float* loss_part;     // per forward block
+    float* grad_part;     // [kWgMaxBlocks][kMParams]
+    float* grad;          // [kMParams]
+    float* loss;          // [1]
+};
+
+// ------------------------------------------------------------ device math
+
+__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * erfcf(-u * 0.70710678118654752f); }
+__device__ __forceinline__ float gelu_d(float u) {
+    return 0.5f * erfcf(-u * 0.70710678118654752f) + u * 0.39894228040143268f * expf(-0.5f * u * u);
+}
+__device__ __forceinline__ unsigned int pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned int*>(&v);
+}
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// D += A B for one 16x8x16 tile (A row-major 16x16, B col-major 16x8, bf16; D f32).
+__device__ __forceinline__ void mma_bf16(float c[4], unsigned int a0, unsigned int a1, unsigned int a2, unsigned int a3,
+                                         unsigned int b0, unsigned int b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned int ld_bf16x2(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned int*>(p); }
+
+// Weights a block keeps in shared memory.
+struct MlpSmem {
+    __nv_bfloat16 W2b[kMHid * kMHid];
+    __nv_bfloat16 W2Tb[kMHid * kMHid];
+    float small[kMSmall];
+};
+
+__device__ __forceinline__ void load_weights(const MlpDev& M, MlpSmem& S, bool need_T) {
+    const unsigned int* src = reinterpret_cast<const unsigned int*>(M.W2b);
+    unsigned int* dst = reinterpret_cast<unsigned int*>(S.W2b);
+    for (int i = threadIdx.x; i < kMHid * kMHid / 2; i += blockDim.x) dst[i] = src[i];
+    if (need_T) {
+        src = reinterpret_cast<const unsigned int*>(M.W2Tb);
+        dst = reinterpret_cast<unsigned int*>(S.W2Tb);
+        for (int i = threadIdx.x; i < kMHid * kMHid / 2; i += blockDim.x) dst[i] = src[i];
+    }
+    for (int i = threadIdx.x; i < kMSmall; i += blockDim.x) S.small[i] = M.small[i];
+    __syncthreads();
+}
+
+// Per-warp forward pass of 16 samples.  Thread (g = lane/4, t = lane%4)
+// holds rows g and g+8 (h = 0, 1) and, for every 8-column tile nt, columns
+// nt*8 + 2t + e (e = 0, 1): element [nt][2h + e] of z1 / z2 (the m16n8
+// accumulator layout, which is also the A-operand layout of the next GEMM).
+struct Tile {
+    float z1[8][4];
+    float z2[8][4];
+    float out[2][2];
+};
+
+__device__ __forceinline__ void tile_forward(const MlpSmem& S, const float x[2][kMIn], Tile& T) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // layer 1 on the CUDA cores
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int col = nt * 8 + 2 * t + e;
+            const float* w = S.small + sW1 + col * kMIn;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float z = S.small[sb1 + col];
+#pragma unroll
+                for (int i = 0; i < kMIn; ++i) z = fmaf(w[i], x[h][i], z);
+                T.z1[nt][2 * h + e] = z;
+            }
+        }
+    }
+    // layer 2 on the tensor cores: A = bf16(gelu(z1)) (16 x 64), B = W2^T
+    unsigned int a[4][4];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb) {
+        a[kb][0] = pack_bf16(gelu_f(T.z1[2 * kb][0]), gelu_f(T.z1[2 * kb][1]));
+        a[kb][1] = pack_bf16(gelu_f(T.z1[2 * kb][2]), gelu_f(T.z1[2 * kb][3]));
+        a[kb][2] = pack_bf16(gelu_f(T.z1[2 * kb + 1][0]), gelu_f(T.z1[2 * kb + 1][1]));
+        a[kb][3] = pack_bf16(gelu_f(T.z1[2 * kb + 1][2]), gelu_f(T.z1[2 * kb + 1][3]));
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        const __nv_bfloat16* wrow = S.W2b + (nt * 8 + g) * kMHid + 2 * t;
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb)
+            mma_bf16(c, a[kb][0], a[kb][1], a[kb][2], a[kb][3], ld_bf16x2(wrow + kb * 16), ld_bf16x2(wrow + kb * 16 + 8));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T.z2[nt][q] = c[q] + S.small[sb2 + nt * 8 + 2 * t + (q & 1)];
+    }
+    // layer 3 on the CUDA cores, reduced over the four threads of a row group
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int o = 0; o < kMOut; ++o) {
+            float s = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                    s = fmaf(S.small[sW3 + o * kMHid + nt * 8 + 2 * t + e], round_bf16(gelu_f(T.z2[nt][2 * h + e])), s);
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            T.out[h][o] = s + S.small[sb3 + o];
+        }
+    }
+}
+
+// Sample index of batch row s: ((first + s) * mul) mod n_data (a permutation
+// of the data set when mul is coprime with n_data).
+__device__ __forceinline__ long long sample_index(long long s, long long first, long long mul, long long n_data) {
+    return (long long)(((unsigned long long)(first + s) % (unsigned long long)n_data) * (unsigned long long)mul %
+                       (unsigned long long)n_data);
+}
+
+// ------------------------------------------------------------ kernels
+
+// Inference (Y != nullptr, T == nullptr) or the per-sample part of training
+// (T != nullptr): one warp per 16 batch rows, grid-stride over tiles.
+__global__ void __launch_bounds__(kFbThreads) k_mlp_fwd_bwd(MlpDev M, const float* __restrict__ X,
+                                                            const float* __restrict__ Y, float* __restrict__ out,
+                                                            long long B, long long first, long long mul,
+                                                            long long n_data, float invB) {
+    __shared__ MlpSmem S;
+    __shared__ float s_loss[kFbThreads / 32];
+    const bool train = Y != nullptr;
+    load_weights(M, S, train);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const long long tiles = (B + 15) / 16;
+    float loss = 0.f;
+    for (long long tile = (long long)blockIdx.x * (kFbThreads / 32) + w; tile < tiles;
+         tile += (long long)gridDim.x * (kFbThreads / 32)) {
+        long long s_row[2];
+        bool valid[2];
+        long long idx[2];
+        float x[2][kMIn];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            s_row[h] = tile * 16 + g + 8 * h;
+            valid[h] = s_row[h] < B;
+            idx[h] = valid[h] ? sample_index(s_row[h], first, mul, n_data) : 0;
+#pragma unroll
+            for (int i = 0; i < kMIn; ++i) x[h][i] = valid[h] ? X[idx[h] * kMIn + i] : 0.f;
+        }
+        Tile T;
+        tile_forward(S, x, T);
+        if (!train) {
+            if (t == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (valid[h]) {
+                        out[s_row[h] * kMOut] = T.out[h][0];
+                        out[s_row[h] * kMOut + 1] = T.out[h][1];
+                    }
+            }
+            continue;
+        }
+        // ---- backward of this tile
+        float dout[2][kMOut];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int o = 0; o < kMOut; ++o) {
+                const float d = valid[h] ? T.out[h][o] - Y[idx[h] * kMOut + o] : 0.f;
+                if (t == 0) loss = fmaf(d, d, loss);
+                dout[h][o] = d * invB;
+            }
+        // dz2 = (dout W3) gelu'(z2), kept in the accumulator layout
+        float dz2[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int col = nt * 8 + 2 * t + (q & 1), h = q >> 1;
+                const float dh = fmaf(S.small[sW3 + kMHid + col], dout[h][1], S.small[sW3 + col] * dout[h][0]);
+                dz2[nt][q] = dh * gelu_d(T.z2[nt][q]);
+            }
+        // per-sample records for the weight gradients
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!valid[h]) continue;
+            const long long s = s_row[h];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = nt * 8 + 2 * t;
+                *reinterpret_cast<float2*>(M.dz2 + s * kMHid + col) = make_float2(dz2[nt][2 * h], dz2[nt][2 * h + 1]);
+                *reinterpret_cast<__nv_bfloat162*>(M.h1b + s * kMHid + col) =
+                    __floats2bfloat162_rn(gelu_f(T.z1[nt][2 * h]), gelu_f(T.z1[nt][2 * h + 1]));
+                *reinterpret_cast<__nv_bfloat162*>(M.h2b + s * kMHid + col) =
+                    __floats2bfloat162_rn(gelu_f(T.z2[nt][2 * h]), gelu_f(T.z2[nt][2 * h + 1]));
+            }
+            if (t == 0) {
+                M.dout[s * kMOut] = dout[h][0];
+                M.dout[s * kMOut + 1] = dout[h][1];
+#pragma unroll
+                for (int i = 0; i < kMIn; ++i) M.xs[s * kMIn + i] = x[h][i];
+            }
+        }
+        // dh1 = bf16(dz2) W2 on the tensor cores: A = bf16(dz2) (16 x 64), B[j][k] = W2[j][k]
+        unsigned int a[4][4];
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) {
+            a[kb][0] = pack_bf16(dz2[2 * kb][0], dz2[2 * kb][1]);
+            a[kb][1] = pack_bf16(dz2[2 * kb][2], dz2[2 * kb][3]);
+            a[kb][2] = pack_bf16(dz2[2 * kb + 1][0], dz2[2 * kb + 1][1]);
+            a[kb][3] = pack_bf16(dz2[2 * kb + 1][2], dz2[2 * kb + 1][3]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            const __nv_bfloat16* wrow = S.W2Tb + (nt * 8 + g) * kMHid + 2 * t;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb)
+                mma_bf16(c, a[kb][0], a[kb][1], a[kb][2], a[kb][3], ld_bf16x2(wrow + kb * 16),
+                         ld_bf16x2(wrow + kb * 16 + 8));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!valid[h]) continue;
+                const int col = nt * 8 + 2 * t;
+                *reinterpret_cast<float2*>(M.dz1 + s_row[h] * kMHid + col) =
+                    make_float2(c[2 * h] * gelu_d(T.z1[nt][2 * h]), c[2 * h + 1] * gelu_d(T.z1[nt][2 * h + 1]));
+            }
+        }
+    }
+    if (!train) return;
+    // loss partial of this block (fixed reduction order)
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, d);
+    if (lane == 0) s_loss[w] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < kFbThreads / 32; ++i) s += s_loss[i];
+        M.loss_part[blockIdx.x] = 0.5f * s * invB;
+    }
+}
+
+// Weight gradients of a batch: block b sums samples [b chunk, (b+1) chunk)
+// into grad_part[b].  dW2 = bf16(dz2)^T h1b runs on the tensor cores: warp w
+// owns rows j = 16w..16w+15 of dW2 and all 64 columns k; a staged tile of 64
+// samples is the reduction dimension (4 k16 steps).
+__global__ void __launch_bounds__(kWgThreads) k_mlp_wgrad(MlpDev M, long long B, long long chunk) {
+    __shared__ __nv_bfloat16 T2[kMHid][kWgTile + 8];  // bf16(dz2)^T: [j][s] (padded rows)
+    __shared__ __nv_bfloat16 H1[kMHid][kWgTile + 8];  // h1b^T: [k][s]
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const long long s_begin = (long long)blockIdx.x * chunk;
+    const long long s_end = s_begin + chunk < B ? s_begin + chunk : B;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+    for (long long s0 = s_begin; s0 < s_end; s0 += kWgTile) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kWgTile * kMHid; idx += blockDim.x) {
+            const int s = idx / kMHid, j = idx % kMHid;
+            const long long ss = s0 + s;
+            const bool ok = ss < s_end;
+            T2[j][s] = __float2bfloat16_rn(ok ? M.dz2[ss * kMHid + j] : 0.f);
+            H1[j][s] = ok ? M.h1b[ss * kMHid + j] : __float2bfloat16_rn(0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kWgTile / 16; ++ks) {
+            const int c0 = ks * 16 + 2 * t;
+            const unsigned int a0 = ld_bf16x2(&T2[16 * w + g][c0]);
+            const unsigned int a1 = ld_bf16x2(&T2[16 * w + g + 8][c0]);
+            const unsigned int a2 = ld_bf16x2(&T2[16 * w + g][c0 + 8]);
+            const unsigned int a3 = ld_bf16x2(&T2[16 * w + g + 8][c0 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+                mma_bf16(acc[nt], a0, a1, a2, a3, ld_bf16x2(&H1[nt * 8 + g][c0]), ld_bf16x2(&H1[nt * 8 + g][c0 + 8]));
+        }
+    }
+    float* part = M.grad_part + (size_t)blockIdx.x * kMParams;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 16 * w + g + 8 * (q >> 1), k = nt * 8 + 2 * t + (q & 1);
+            part[oW2 + j * kMHid + k] = acc[nt][q];
+        }
+    // the small gradients on the CUDA cores, one column per thread
+    const int tid = threadIdx.x;
+    if (tid < kMHid) {
+        const int j = tid;
+        float gw[kMIn] = {0.f, 0.f, 0.f, 0.f, 0.f}, gb1 = 0.f, gb2 = 0.f;
+        for (long long s = s_begin; s < s_end; ++s) {
+            const float d1 = M.dz1[s * kMHid + j];
+#pragma unroll
+            for (int i = 0; i < kMIn; ++i) gw[i] = fmaf(d1, M.xs[s * kMIn + i], gw[i]);
+            gb1 += d1;
+            gb2 += M.dz2[s * kMHid + j];
+        }
+#pragma unroll
+        for (int i = 0; i < kMIn; ++i) part[oW1 + j * kMIn + i] = gw[i];
+        part[ob1 + j] = gb1;
+        part[ob2 + j] = gb2;
+    } else {
+        const int j = tid - kMHid;
+        float g0 = 0.f, g1 = 0.f, d0 = 0.f, d1 = 0.f;
+        for (long long s = s_begin; s < s_end; ++s) {
+            const float h = __bfloat162float(M.h2b[s * kMHid + j]);
+            const float o0 = M.dout[s * kMOut], o1 = M.dout[s * kMOut + 1];
+            g0 = fmaf(o0, h, g0);
+            g1 = fmaf(o1, h, g1);
+            d0 += o0;
+            d1 += o1;
+        }
+        part[oW3 + j] = g0;
+        part[oW3 + kMHid + j] = g1;
+        if (j == 0) {
+            part[ob3] = d0;
+            part[ob3 + 1] = d1;
+        }
+    }
+}
+
+struct AdamArgs {
+    float lr, beta1, beta2, eps, c1, c2;  // c1, c2: bias corrections 1/(1 - beta^t)
+    int apply;                            // 0: gradients only
+};
+
+// Sums the partials of n_part blocks in block order, writes the gradient and
+// the batch loss, applies Adam to the masters and refreshes the rounded copies.
+__global__ void k_mlp_update(MlpDev M, int n_part, int n_loss, AdamArgs A) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        float s = 0.f;
+        for (int b = 0; b < n_loss; ++b) s += M.loss_part[b];
+        *M.loss = s;
+    }
+    if (p >= kMParams) return;
+    float gsum = 0.f;
+    for (int b = 0; b < n_part; ++b) gsum += M.grad_part[(size_t)b * kMParams + p];
+    M.grad[p] = gsum;
+    if (!A.apply) return;
+    const float m = A.beta1 * M.m[p] + (1.f - A.beta1) * gsum;
+    const float v = A.beta2 * M.v[p] + (1.f - A.beta2) * gsum * gsum;
+    M.m[p] = m;
+    M.v[p] = v;
+    const float w = M.master[p] - A.lr * (m * A.c1) / (sqrtf(v * A.c2) + A.eps);
+    M.master[p] = w;
+}
+
+// bf16 / compact copies of the masters.
+__global__ void k_mlp_refresh(MlpDev M) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kMParams) return;
+    const float w = M.master[p];
+    if (p >= oW2 && p < ob2) {
+        const int j = (p - oW2) / kMHid, k = (p - oW2) % kMHid;
+        const __nv_bfloat16 b = __float2bfloat16_rn(w);
+        M.W2b[j * kMHid + k] = b;
+        M.W2Tb[k * kMHid + j] = b;
+    } else if (p < ob1) {
+        M.small[sW1 + p] = round_bf16(w);
+    } else if (p < oW2) {
+        M.small[sb1 + (p - ob1)] = w;
+    } else if (p < oW3) {
+        M.small[sb2 + (p - ob2)] = w;
+    } else if (p < ob3) {
+        M.small[sW3 + (p - oW3)] = round_bf16(w);
+    } else {
+        M.small[sb3 + (p - ob3)] = w;
+    }
+}
+
+}  // namespace pic
+
+// ------------------------------------------------------------ C ABI
+
+struct pic_mlp {
+    pic::MlpDev D;
+    long long max_batch = 0;
+    cudaStream_t st = nullptr;
+    int sm_count = 0;
+    long long t = 0;  // Adam steps taken
+    std::vector<void*> allocs;
+    float* loss_host = nullptr;  // pinned
+};
+
+namespace {
+
+int mlp_map(cudaError_t e) {
+    if (e == cudaSuccess) return PIC_OK;
+    if (e == cudaErrorMemoryAllocation) return PIC_ERR_NO_MEMORY;
+    return PIC_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t mlp_alloc(pic_mlp* m, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) m->allocs.push_back(q);
+    *p = (T*)q;
+    return e;
+}
+
+void mlp_free(pic_mlp* m) {
+    for (void* p : m->allocs) cudaFree(p);
+    m->allocs.clear();
+    if (m->loss_host) cudaFreeHost(m->loss_host);
+    m->loss_host = nullptr;
+}
+
+int fb_grid(const pic_mlp* m, long long B) {
+    const long long tiles = (B + 15) / 16;
+    long long g = (tiles + 3) / 4;
+    const long long cap = (long long)m->sm_count * 8;
+    return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+// Forward + backward + weight gradients + reduction (+ Adam when apply).
+cudaError_t mlp_step(pic_mlp* m, long long B, const float* X, const float* Y, long long first, long long mul,
+                     long long n_data, int apply, const pic_adam_t* opt) {
+    pic::MlpDev& D = m->D;
+    const int gf = fb_grid(m, B);
+    pic::k_mlp_fwd_bwd<<<gf, pic::kFbThreads, 0, m->st>>>(D, X, Y, nullptr, B, first, mul, n_data, 1.0f / (float)B);
+    long long nwg = (B + pic::kWgTile - 1) / pic::kWgTile;
+    if (nwg > pic::kWgMaxBlocks) nwg = pic::kWgMaxBlocks;
+    long long chunk = (B + nwg - 1) / nwg;
+    chunk = (chunk + pic::kWgTile - 1) / pic::kWgTile * pic::kWgTile;
+    nwg = (B + chunk - 1) / chunk;
+    pic::k_mlp_wgrad<<<(int)nwg, pic::kWgThreads, 0, m->st>>>(D, B, chunk);
+    pic::AdamArgs A;
+    std::memset(&A, 0, sizeof(A));
+    if (apply) {
+        m->t += 1;
+        A.lr = opt->lr;
+        A.beta1 = opt->beta1;
+        A.beta2 = opt->beta2;
+        A.eps = opt->eps;
+        A.c1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)m->t)));
+        A.c2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)m->t)));
+        A.apply = 1;
+    }
+    const int gp = (pic::kMParams + 255) / 256;
+    pic::k_mlp_update<<<gp, 256, 0, m->st>>>(D, (int)nwg, gf, A);
+    if (apply) pic::k_mlp_refresh<<<gp, 256, 0, m->st>>>(D);
+    return cudaGetLastError();
+}
+
+long long gcd_ll(long long a, long long b) {
+    while (b) {
+        const long long r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+}  // namespace
+
+// The learned stepper reads the model's device weights (mlp.cu and api.cu).
+namespace pic {
+const MlpDev* mlp_device(const pic_mlp* m) { return m ? &m->D : nullptr; }
+cudaStream_t mlp_stream(const pic_mlp* m) { return m ? m->st : nullptr; }
+}  // namespace pic
+
+extern "C" {
+
+int pic_mlp_num_params(void) { return pic::kMParams; }
+
+int pic_mlp_create(int64_t max_batch, void* stream, pic_mlp** out) {
+    if (!out || max_batch < 1 || max_batch > (1ll << 26)) return PIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0, sms = 0, count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) return PIC_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PIC_ERR_CUDA;
+    pic_mlp* m = new (std::nothrow) pic_mlp();
+    if (!m) return PIC_ERR_NO_MEMORY;
+    m->max_batch = max_batch;
+    m->st = (cudaStream_t)stream;
+    m->sm_count = sms;
+    pic::MlpDev& D = m->D;
+    std::memset(&D, 0, sizeof(D));
+    const size_t B = (size_t)max_batch;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.master, pic::kMParams);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.m, pic::kMParams);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.v, pic::kMParams);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.W2b, pic::kMHid * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.W2Tb, pic::kMHid * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.small, pic::kMSmall);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.xs, B * pic::kMIn);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.dz1, B * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.dz2, B * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.h1b, B * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.h2b, B * pic::kMHid);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.dout, B * pic::kMOut);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.loss_part, (size_t)sms * 8);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.grad_part, (size_t)pic::kWgMaxBlocks * pic::kMParams);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.grad, pic::kMParams);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.loss, 1);
+    if (e == cudaSuccess) e = cudaMallocHost(&m->loss_host, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.master, 0, sizeof(float) * pic::kMParams, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.m, 0, sizeof(float) * pic::kMParams, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.v, 0, sizeof(float) * pic::kMParams, m->st);
+    if (e == cudaSuccess) {
+        pic::k_mlp_refresh<<<(pic::kMParams + 255) / 256, 256, 0, m->st>>>(D);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) {
+        mlp_free(m);
+        delete m;
+        return mlp_map(e);
+    }
+    *out = m;
+    return PIC_OK;
+}
+
+int pic_mlp_set_weights(pic_mlp* m, const float* w, int ptr_kind) {
+    if (!m || !w || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(m->D.master, w, sizeof(float) * pic::kMParams,
+                                    ptr_kind == PIC_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->D.m, 0, sizeof(float) * pic::kMParams, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->D.v, 0, sizeof(float) * pic::kMParams, m->st);
+    if (e == cudaSuccess) {
+        pic::k_mlp_refresh<<<(pic::kMParams + 255) / 256, 256, 0, m->st>>>(m->D);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    m->t = 0;
+    return mlp_map(e);
+}
+
+int pic_mlp_get_weights(pic_mlp* m, float* w, int ptr_kind) {
+    if (!m || !w || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(w, m->D.master, sizeof(float) * pic::kMParams,
+                                    ptr_kind == PIC_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    return mlp_map(e);
+}
+
+int pic_mlp_forward(pic_mlp* m, int64_t n, const float* X_dev, float* Y_dev) {
+    if (!m || n < 0 || (n > 0 && (!X_dev || !Y_dev))) return PIC_ERR_INVALID_ARG;
+    if (n == 0) return PIC_OK;
+    pic::k_mlp_fwd_bwd<<<fb_grid(m, n), pic::kFbThreads, 0, m->st>>>(m->D, X_dev, nullptr, Y_dev, n, 0, 1, n, 1.0f);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    return mlp_map(e);
+}
+
+int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_dev, float* grad, float* loss,
+                      int ptr_kind) {
+    if (!m || n < 1 || n > m->max_batch || !X_dev || !T_dev || !grad || !loss) return PIC_ERR_INVALID_ARG;
+    if (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE) return PIC_ERR_INVALID_ARG;
+    const cudaMemcpyKind k = ptr_kind == PIC_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = mlp_step(m, n, X_dev, T_dev, 0, 1, n, 0, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad, m->D.grad, sizeof(float) * pic::kMParams, k, m->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, m->D.loss, sizeof(float), k, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    return mlp_map(e);
+}
+
+int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T_dev, int64_t batch, int64_t steps,
+                  const pic_adam_t* opt, uint64_t seed, float* loss_hist) {
+    if (!m || !opt || n_data < 1 || batch < 1 || batch > m->max_batch || batch > n_data || steps < 0 || !X_dev ||
+        !T_dev)
+        return PIC_ERR_INVALID_ARG;
+    if (!(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) ||
+        !(opt->eps > 0.f))
+        return PIC_ERR_INVALID_ARG;
+    // a multiplier coprime with n_data: the batches walk a fixed permutation
+    long long mul = (long long)(seed % (uint64_t)n_data) | 1ll;
+    if (mul < 2) mul = n_data > 2 ? n_data / 2 + 1 : 1;
+    while (gcd_ll(mul, n_data) != 1) ++mul;
+    cudaError_t e = cudaSuccess;
+    for (long long s = 0; s < steps && e == cudaSuccess; ++s) {
+        const long long first = (s * batch) % n_data;
+        e = mlp_step(m, batch, X_dev, T_dev, first, mul, n_data, 1, opt);
+        if (e == cudaSuccess && loss_hist) {
+            e = cudaMemcpyAsync(m->loss_host, m->D.loss, sizeof(float), cudaMemcpyDeviceToHost, m->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+            if (e == cudaSuccess) loss_hist[s] = *m->loss_host;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    return mlp_map(e);
+}
+
+void pic_mlp_destroy(pic_mlp* m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->st);
+    mlp_free(m);
+    delete m;
+}
+
+}  // extern "C"

@@ -38,6 +38,10 @@ class PicError(RuntimeError):
         super().__init__(f"{what}: {pic_strerror(status)} (status {status})")
 
 
+class pic_adam_t(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class pic_params(C.Structure):
     _fields_ = [
         ("eps", C.c_double),
@@ -137,6 +141,14 @@ def load() -> C.CDLL:
             "pic_poisson_noalloc": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
             "pic_test_barrier_timeout": (i32, [i64, i32, vp]),
+            "pic_mlp_num_params": (i32, []),
+            "pic_mlp_create": (i32, [i64, vp, P(vp)]),
+            "pic_mlp_set_weights": (i32, [vp, vp, i32]),
+            "pic_mlp_get_weights": (i32, [vp, vp, i32]),
+            "pic_mlp_forward": (i32, [vp, i64, vp, vp]),
+            "pic_mlp_gradients": (i32, [vp, i64, vp, vp, vp, vp, i32]),
+            "pic_mlp_train": (i32, [vp, i64, vp, vp, i64, i64, P(pic_adam_t), C.c_uint64, vp]),
+            "pic_mlp_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -339,3 +351,67 @@ def pic_gather(params: pic_params, R_dev, E_dev, edges_dev, e_dev, stream=None) 
 def pic_test_barrier_timeout(wait_limit_ns: int, stream=None, precision: int = 0) -> int:
     """Returns the raw status (PIC_ERR_TIMEOUT expected)."""
     return int(load().pic_test_barrier_timeout(wait_limit_ns, precision, _stream(stream)))
+
+
+# ------------------------------------------------------------ learned stepper
+
+PIC_MLP_PARAMS = 4674
+
+
+class Mlp:
+    """Owner of a pic_mlp*; pic_mlp_destroy runs when it is closed or collected."""
+
+    def __init__(self, ptr: int, max_batch: int):
+        self.ptr = C.c_void_p(ptr)
+        self.max_batch = max_batch
+
+    def close(self):
+        if self.ptr:
+            load().pic_mlp_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pic_mlp_create(max_batch: int, stream=None) -> Mlp:
+    out = C.c_void_p()
+    _check(load().pic_mlp_create(int(max_batch), _stream(stream), C.byref(out)), "pic_mlp_create")
+    return Mlp(out.value, int(max_batch))
+
+
+def pic_mlp_set_weights(m: Mlp, w) -> None:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == PIC_MLP_PARAMS
+    _check(load().pic_mlp_set_weights(m.ptr, w.ctypes.data, PIC_PTR_HOST), "pic_mlp_set_weights")
+
+
+def pic_mlp_get_weights(m: Mlp) -> np.ndarray:
+    w = np.empty(PIC_MLP_PARAMS, np.float32)
+    _check(load().pic_mlp_get_weights(m.ptr, w.ctypes.data, PIC_PTR_HOST), "pic_mlp_get_weights")
+    return w
+
+
+def pic_mlp_forward(m: Mlp, X_dev, Y_dev) -> None:
+    """X_dev: n x 5 float32 device tensor; Y_dev: n x 2 float32 device tensor."""
+    _check(load().pic_mlp_forward(m.ptr, int(X_dev.shape[0]), _ptr(X_dev)[0], _ptr(Y_dev)[0]), "pic_mlp_forward")
+
+
+def pic_mlp_gradients(m: Mlp, X_dev, T_dev):
+    g = np.empty(PIC_MLP_PARAMS, np.float32)
+    loss = np.empty(1, np.float32)
+    _check(load().pic_mlp_gradients(m.ptr, int(X_dev.shape[0]), _ptr(X_dev)[0], _ptr(T_dev)[0], g.ctypes.data,
+                                    loss.ctypes.data, PIC_PTR_HOST), "pic_mlp_gradients")
+    return g, float(loss[0])
+
+
+def pic_mlp_train(m: Mlp, X_dev, T_dev, batch: int, steps: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  seed: int = 0) -> np.ndarray:
+    opt = pic_adam_t(lr, beta1, beta2, eps)
+    hist = np.empty(max(int(steps), 1), np.float32)
+    _check(load().pic_mlp_train(m.ptr, int(X_dev.shape[0]), _ptr(X_dev)[0], _ptr(T_dev)[0], int(batch), int(steps),
+                                C.byref(opt), C.c_uint64(seed), hist.ctypes.data), "pic_mlp_train")
+    return hist[:int(steps)]

@@ -1,0 +1,123 @@
+"""The learned stepper's network on the GPU against its FP64 oracle.
+
+The GPU evaluates the network with bfloat16 weights and hidden activations
+and FP32 accumulation; the oracle evaluates the same formulas in FP64 with
+the same bfloat16 rounding points (oracle/mlp.py).  They can then differ by
+FP32 rounding (relative ~1e-6) and, rarely, by one bfloat16 ulp (2^-8 |h|) of
+a hidden activation whose FP32 and FP64 values straddle a rounding boundary.
+One such flip moves an output by at most max|W3| max gelu' max|W2| 2^-8
+max|h| <= 0.3 x 1.13 x 0.3 x 2^-8 x 8 ~ 3e-3 with the weights and inputs used
+here (|h| <= 8 for inputs of spread 1.5).  A sample has 128 rounding points;
+each flips with probability about (FP32 - FP64 discrepancy, a few 2^-24) /
+(bfloat16 ulp, 2^-8), so about 128 x 4 x 2^-16 ~ 1 % of the samples carry a
+flip.  So: outputs within 1e-2, at most 2 % of them beyond 1e-5; gradients,
+averages over the batch, within 2e-3 of the largest entry of each block.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1404_1160_gb300 import inputs
+from paper_1404_1160_gb300 import pic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_1160_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def batch(n, seed):
+    rng = np.random.default_rng(seed)
+    X = np.stack([rng.normal(0, 1.5, n), rng.normal(0, 1.5, n), np.sin(rng.uniform(0, 6.3, n)),
+                  np.cos(rng.uniform(0, 6.3, n)), np.full(n, 0.4)], axis=1).astype(np.float32)
+    T = np.stack([0.3 * np.sin(X[:, 0]) * X[:, 1], 0.2 * np.cos(X[:, 1]) - 0.1 * X[:, 0] * X[:, 3]], axis=1)
+    return X, T.astype(np.float32)
+
+
+def weights(seed, scale=1.0):
+    w = inputs.mlp_init(seed)
+    rng = np.random.default_rng(seed + 100)
+    # nonzero biases too, so that every parameter block is exercised
+    p = omlp.unflatten(w.astype(np.float64))
+    for b in ("b1", "b2", "b3"):
+        p[b] = rng.normal(0, 0.1, p[b].shape)
+    return (omlp.flatten(p) * scale).astype(np.float32)
+
+
+@pytest.mark.parametrize("n", [1, 17, 4096, 100_003])
+def test_forward_matches_oracle(n):
+    m = pic.pic_mlp_create(16)
+    w = weights(1)
+    pic.pic_mlp_set_weights(m, w)
+    X, _ = batch(n, 2)
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    pic.pic_mlp_forward(m, dev(X), Y)
+    ref = omlp.forward(w.astype(np.float64), X.astype(np.float64))["out"]
+    err = np.abs(Y.cpu().numpy() - ref)
+    assert err.max() <= 1e-2, err.max()
+    assert np.mean(err > 1e-5) <= 2e-2, np.mean(err > 1e-5)
+    assert np.array_equal(pic.pic_mlp_get_weights(m), w)
+    m.close()
+
+
+@pytest.mark.parametrize("n", [16, 1000, 8192])
+def test_gradients_match_oracle(n):
+    m = pic.pic_mlp_create(n)
+    w = weights(3)
+    pic.pic_mlp_set_weights(m, w)
+    X, T = batch(n, 4)
+    g, loss = pic.pic_mlp_gradients(m, dev(X), dev(T))
+    loss_o, g_o = omlp.loss_and_grads(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - loss_o) <= 1e-4 * max(1.0, loss_o)
+    for name, shape in omlp.SHAPES:
+        k0 = sum(int(np.prod(s)) for nm, s in omlp.SHAPES[:[x[0] for x in omlp.SHAPES].index(name)])
+        k1 = k0 + int(np.prod(shape))
+        ref = g_o[k0:k1]
+        err = np.abs(g[k0:k1] - ref).max()
+        assert err <= 2e-3 * np.abs(ref).max() + 1e-9, (name, err, np.abs(ref).max())
+    # reproducible bit for bit
+    g2, loss2 = pic.pic_mlp_gradients(m, dev(X), dev(T))
+    assert np.array_equal(g, g2) and loss == loss2
+    m.close()
+
+
+def test_training_reduces_loss_and_is_reproducible():
+    X, T = batch(40_000, 5)
+    Xd, Td = dev(X), dev(T)
+    runs = []
+    for _ in range(2):
+        m = pic.pic_mlp_create(2048)
+        pic.pic_mlp_set_weights(m, inputs.mlp_init(7))
+        hist = pic.pic_mlp_train(m, Xd, Td, batch=2048, steps=400, lr=3e-3, seed=11)
+        runs.append((hist, pic.pic_mlp_get_weights(m)))
+        m.close()
+    hist, w = runs[0]
+    assert np.all(np.isfinite(hist))
+    assert hist[-20:].mean() < 0.05 * hist[:5].mean(), (hist[:5].mean(), hist[-20:].mean())
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][0], runs[1][0])
+    # the trained weights evaluated by the oracle fit the held-out data too
+    Xh, Th = batch(5000, 6)
+    out = omlp.forward(w.astype(np.float64), Xh.astype(np.float64))["out"]
+    assert np.mean((out - Th) ** 2) < 0.1 * np.mean(Th ** 2)
+
+
+def test_argument_checks():
+    with pytest.raises(pic.PicError):
+        pic.pic_mlp_create(0)
+    m = pic.pic_mlp_create(8)
+    X, T = batch(16, 1)
+    with pytest.raises(pic.PicError):
+        pic.pic_mlp_gradients(m, dev(X), dev(T))  # more samples than max_batch
+    m.close()
