@@ -130,6 +130,13 @@ int pic_step(pic_handle* h, int64_t n_steps);
    paper's reference solution (Sec. 2.1, RK4 with step 2*pi*eps/100). */
 int pic_fine_steps(pic_handle* h, int64_t n_fine);
 
+/* The paper's reference solution over a time t (Sec. 2.1): floor(t/h) fine
+   steps of h = 2 pi eps / steps_per_turn and one last step of the remainder,
+   with the configured fine solver and field.  FP64 handles only
+   (PIC_ERR_UNSUPPORTED for precision 1, whose rotation tables hold the
+   multiples of h only). */
+int pic_fine_advance(pic_handle* h, double t);
+
 typedef struct {
     double  t;                 /* time reached                                  */
     int64_t n_steps;           /* macro steps taken                             */
@@ -291,6 +298,23 @@ int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_
 int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T_dev, int64_t batch, int64_t steps,
                   const pic_adam_t* opt, uint64_t seed, float* loss_hist);
 void pic_mlp_destroy(pic_mlp* m);
+
+/* n_steps macro steps of the learned stepper on a handle.  Each step:
+   (1) y^n is kept and, with the Poisson model, the field E of y^n is frozen
+   with its potential psi (psi' = E, psi(0) = 0; E = rE_edge/r off the mesh);
+   (2) the plain improved-ETD step of pic_step gives y_plain;
+   (3) y_learned = y_plain + (scale_R, scale_V) * network(R^n, V^n,
+   sin(t_n/eps), cos(t_n/eps), dt), the network's output scaled per
+   component;
+   (4) each particle keeps y_learned when its frozen-field energy
+   H = (R^2 + V^2)/2 - eps psi(R) (psi = -R^4/4 for the Duffing field, 0
+   for the zero field) differs from that of y_plain by at most
+   drift_tol |H(y_plain)| (the plain step judges the correction), and the
+   plain step otherwise.  A zero correction leaves y_plain.  *n_fallback (may be NULL) receives the
+   number of particle-steps that kept the plain step.  The network is only
+   read.  Synchronises the handle's stream. */
+int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float scale_R, float scale_V,
+                     double drift_tol, int64_t* n_fallback);
 
 /* ---- testing ------------------------------------------------------------ */
 /* Runs one macro step of a small Poisson beam (in the given precision, 0 or

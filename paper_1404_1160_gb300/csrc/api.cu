@@ -134,6 +134,22 @@ void make_devparams(const pic_params* p, long long n, DevParams* d) {
     d->rot = nullptr;
 }
 
+// Fine-step constants for a step of size hstep (the same formulas as
+// make_devparams, which uses hstep = 2 pi eps / steps_per_turn).
+void set_fine_step(DevParams* d, double eps, double hstep) {
+    d->h = hstep;
+    d->h2 = 0.5 * hstep;
+    d->h6 = hstep / 6.0;
+    const double th = hstep / eps;
+    d->c1 = std::cos(th);
+    d->s1 = std::sin(th);
+    d->ch = std::cos(0.5 * th);
+    d->sh = std::sin(0.5 * th);
+    d->hsh = hstep * d->sh;
+    d->tch = 2.0 * d->ch;
+    d->tsh = 2.0 * d->sh;
+}
+
 // Rotation table of the FP32 form: entry m = (cos, sin)(m pi / spt), the
 // exact E = 0 flow over m half fine steps, m = 0 .. 2 spt - 1, in FP64
 // rounded once to binary32.  Entries whose exact value is 0 or +-1 (quarter
@@ -206,6 +222,10 @@ struct pic_handle {
     pic::CTime *Tin32 = nullptr, *Tin32_alt = nullptr;
     float2* rot32 = nullptr;
     pic::SortBufs32 sort32;
+    // learned stepper (allocated by the first pic_step_learned)
+    void* y_prev = nullptr;
+    double* psi = nullptr;
+    unsigned long long* n_fb = nullptr;
     double t = 0.0;
     long long n_steps = 0;
     int have_periods = 0;
@@ -651,6 +671,110 @@ int pic_step(pic_handle* h, int64_t n_steps) {
         h->n_steps += n_steps;
         h->have_periods = 1;
     }
+    return rc;
+}
+
+int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float scale_R, float scale_V,
+                     double drift_tol, int64_t* n_fallback) {
+    if (!h || !m || n_steps < 0 || !(drift_tol >= 0.0) || !std::isfinite(scale_R) || !std::isfinite(scale_V))
+        return PIC_ERR_INVALID_ARG;
+    if (n_fallback) *n_fallback = 0;
+    if (n_steps == 0 || h->n == 0) {
+        if (n_steps > 0 && h->n == 0) {
+            h->t += (double)n_steps * h->prm.dt;
+            h->n_steps += n_steps;
+        }
+        return PIC_OK;
+    }
+    const bool poisson = h->prm.field_model == PIC_FIELD_POISSON;
+    const size_t Np1 = (size_t)h->dp.n_cells + 1;
+    const size_t state_bytes = (size_t)h->n * (h->prec ? sizeof(float2) : sizeof(double2));
+    int rc = PIC_OK;
+    if (!h->y_prev) {
+        char* yp = nullptr;
+        rc = dalloc(h, &yp, state_bytes);
+        if (!rc) h->y_prev = yp;
+        if (!rc) rc = dalloc(h, &h->n_fb, 1);
+        if (!rc && poisson) rc = dalloc(h, &h->psi, Np1);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaMemsetAsync(h->n_fb, 0, sizeof(unsigned long long), h->st);
+    for (long long step = 0; step < n_steps && e == cudaSuccess && rc == PIC_OK; ++step) {
+        // the storage order of this step, then y^n and the field at t_n
+        e = maybe_sort(h, h->n_steps);
+        void* state = h->prec ? (void*)h->B32.y : (void*)h->B.y;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->y_prev, state, state_bytes, cudaMemcpyDeviceToDevice, h->st);
+        if (e == cudaSuccess && poisson) {
+            e = h->prec ? pic::launch_deposit32(h->dp, (const float*)h->B32.y, h->n, 2, h->Qf, h->nout_f, h->st,
+                                                h->sm_count, &h->launches)
+                        : pic::launch_deposit(h->dp, (const double*)h->B.y, h->n, 2, h->Qf, h->nout_f, h->st,
+                                              h->sm_count, &h->launches);
+            if (e == cudaSuccess) e = pic::launch_poisson(h->dp, h->Qf, h->Ef, h->edges_f, h->S, h->st, &h->launches);
+            if (e == cudaSuccess) e = pic::launch_psi_nodes(h->Ef, h->dp.n_cells, h->dp.hr, h->psi, h->st, &h->launches);
+        }
+        if (e != cudaSuccess) break;
+        // the plain improved-ETD step, in the order just fixed
+        const int saved = h->prm.sort_every;
+        h->prm.sort_every = 0;
+        rc = run_window(h, pic::MODE_ETD, 1);
+        h->prm.sort_every = saved;
+        if (rc) break;
+        pic::LearnedArgs A;
+        std::memset(&A, 0, sizeof(A));
+        A.y_prev = h->y_prev;
+        A.y = state;
+        A.n = h->n;
+        A.prec = h->prec;
+        const double phase = h->t / h->prm.eps;
+        A.in_sin = (float)std::sin(phase);
+        A.in_cos = (float)std::cos(phase);
+        A.in_dt = (float)h->prm.dt;
+        A.scale_R = scale_R;
+        A.scale_V = scale_V;
+        A.tol = drift_tol;
+        A.field = h->prm.field_model;
+        A.eps = h->prm.eps;
+        if (poisson) {
+            A.E = h->Ef;
+            A.psi = h->psi;
+            A.edges = h->edges_f;
+            A.r_min = h->dp.r_min;
+            A.hr = h->dp.hr;
+            A.inv_hr = h->dp.inv_hr;
+            A.n_cells = h->dp.n_cells;
+        }
+        A.n_fallback = h->n_fb;
+        e = pic::launch_learned_apply(m, A, h->sm_count, h->st, &h->launches);
+        if (e == cudaSuccess) {
+            h->t += h->prm.dt;
+            h->n_steps += 1;
+            h->have_periods = 1;
+        }
+    }
+    if (rc) return rc;
+    if (e != cudaSuccess) return map_cuda(e);
+    unsigned long long nfb = 0;
+    e = cudaMemcpyAsync(&nfb, h->n_fb, sizeof(nfb), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (n_fallback) *n_fallback = (int64_t)nfb;
+    return PIC_OK;
+}
+
+int pic_fine_advance(pic_handle* h, double t) {
+    if (!h || !(t >= 0.0) || !std::isfinite(t)) return PIC_ERR_INVALID_ARG;
+    if (h->prec) return PIC_ERR_UNSUPPORTED;
+    const long long nfull = (long long)std::floor(t / h->dp.h);
+    const double rem = t - (double)nfull * h->dp.h;
+    int rc = PIC_OK;
+    if (nfull > 0) rc = run_window(h, pic::MODE_FINE, nfull);
+    if (!rc && rem > 0.0) {
+        const DevParams saved = h->dp;
+        set_fine_step(&h->dp, h->prm.eps, rem);
+        rc = run_window(h, pic::MODE_FINE, 1);
+        h->dp = saved;
+    }
+    if (!rc) h->t += t;
     return rc;
 }
 

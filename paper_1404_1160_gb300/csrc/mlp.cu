@@ -432,6 +432,115 @@ __global__ void k_mlp_refresh(MlpDev M) {
     }
 }
 
+// ------------------------------------------------------------ learned step
+
+// Potential psi (psi' = E, psi(0) = 0) of the field the gather sees: E linear
+// in each cell, so psi is quadratic there; off the mesh E = rE_edge / r.
+__device__ __forceinline__ double psi_at(const LearnedArgs& A, double R) {
+    if (A.field == PIC_FIELD_DUFFING) return -0.25 * ((R * R) * (R * R));
+    if (A.field != PIC_FIELD_POISSON) return 0.0;
+    const double x = (R - A.r_min) * A.inv_hr;
+    if (x >= 0.0 && x < (double)A.n_cells) {
+        const int j = (int)floor(x);
+        const double d = R - (A.r_min + (double)j * A.hr);
+        const double Ej = A.E[j], Ej1 = A.E[j + 1];
+        return A.psi[j] + Ej * d + (Ej1 - Ej) * (d * d) * (0.5 * A.inv_hr);
+    }
+    if (x < 0.0) return A.psi[0] + A.edges[0] * log(R / A.r_min);
+    return A.psi[A.n_cells] + A.edges[1] * log(R / -A.r_min);  // beyond r_max (NaN propagates)
+}
+
+// Frozen-field energy (R^2 + V^2)/2 - eps psi(R): conserved by the
+// characteristics dR/dt = V/eps, dV/dt = -R/eps + E(R) when E does not change.
+__device__ __forceinline__ double frozen_energy(const LearnedArgs& A, double R, double V) {
+    return 0.5 * (R * R + V * V) - A.eps * psi_at(A, R);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedArgs A) {
+    __shared__ MlpSmem S;
+    load_weights(M, S, false);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const long long n = A.n, tiles = (n + 15) / 16;
+    unsigned int fallback = 0;
+    for (long long tile = (long long)blockIdx.x * (kFbThreads / 32) + w; tile < tiles;
+         tile += (long long)gridDim.x * (kFbThreads / 32)) {
+        double yp[2][2];
+        bool valid[2];
+        float x[2][kMIn];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long s = tile * 16 + g + 8 * h;
+            valid[h] = s < n;
+            if (PREC == 0) {
+                const double2 v = valid[h] ? ((const double2*)A.y_prev)[s] : make_double2(0.0, 0.0);
+                yp[h][0] = v.x;
+                yp[h][1] = v.y;
+            } else {
+                const float2 v = valid[h] ? ((const float2*)A.y_prev)[s] : make_float2(0.f, 0.f);
+                yp[h][0] = v.x;
+                yp[h][1] = v.y;
+            }
+            x[h][0] = (float)yp[h][0];
+            x[h][1] = (float)yp[h][1];
+            x[h][2] = A.in_sin;
+            x[h][3] = A.in_cos;
+            x[h][4] = A.in_dt;
+        }
+        Tile T;
+        tile_forward(S, x, T);
+        if (t < 2) {
+            const int h = t;
+            const long long s = tile * 16 + g + 8 * h;
+            const double dR = (double)(A.scale_R * T.out[h][0]), dV = (double)(A.scale_V * T.out[h][1]);
+            if (valid[h] && (dR != 0.0 || dV != 0.0)) {
+                double Rp, Vp, Rl, Vl;
+                if (PREC == 0) {
+                    const double2 pl = ((const double2*)A.y)[s];
+                    Rp = pl.x;
+                    Vp = pl.y;
+                    Rl = pl.x + dR;
+                    Vl = pl.y + dV;
+                } else {
+                    const float2 pl = ((const float2*)A.y)[s];
+                    Rp = pl.x;
+                    Vp = pl.y;
+                    Rl = (double)(pl.x + (float)dR);
+                    Vl = (double)(pl.y + (float)dV);
+                }
+                // the plain step judges: the correction may move the frozen-field
+                // energy away from the plain step's by at most tol |H|
+                const double H0 = frozen_energy(A, Rp, Vp);
+                const double H1 = frozen_energy(A, Rl, Vl);
+                if (fabs(H1 - H0) <= A.tol * fabs(H0)) {
+                    if (PREC == 0) ((double2*)A.y)[s] = make_double2(Rl, Vl);
+                    else ((float2*)A.y)[s] = make_float2((float)Rl, (float)Vl);
+                } else {
+                    ++fallback;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) fallback += __shfl_xor_sync(0xffffffffu, fallback, d);
+    if (lane == 0 && fallback) atomicAdd(A.n_fallback, (unsigned long long)fallback);
+}
+
+__global__ void k_psi_nodes(const double* __restrict__ E, int n_cells, double hr, double* __restrict__ psi) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int c = n_cells / 2;
+    psi[c] = 0.0;
+    for (int j = c + 1; j <= n_cells; ++j) psi[j] = psi[j - 1] + (0.5 * hr) * (E[j - 1] + E[j]);
+    for (int j = c - 1; j >= 0; --j) psi[j] = psi[j + 1] - (0.5 * hr) * (E[j] + E[j + 1]);
+}
+
+cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* psi, cudaStream_t st,
+                             long long* launches) {
+    k_psi_nodes<<<1, 32, 0, st>>>(E, n_cells, hr, psi);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
 }  // namespace pic
 
 // ------------------------------------------------------------ C ABI
@@ -518,10 +627,19 @@ long long gcd_ll(long long a, long long b) {
 
 }  // namespace
 
-// The learned stepper reads the model's device weights (mlp.cu and api.cu).
 namespace pic {
-const MlpDev* mlp_device(const pic_mlp* m) { return m ? &m->D : nullptr; }
-cudaStream_t mlp_stream(const pic_mlp* m) { return m ? m->st : nullptr; }
+cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_count, cudaStream_t st,
+                                 long long* launches) {
+    if (A.n == 0) return cudaSuccess;
+    const long long tiles = (A.n + 15) / 16;
+    long long g = (tiles + 3) / 4;
+    const long long cap = (long long)sm_count * 8;
+    const int grid = (int)(g < 1 ? 1 : (g < cap ? g : cap));
+    if (A.prec == 0) k_learned_apply<0><<<grid, kFbThreads, 0, st>>>(m->D, A);
+    else k_learned_apply<1><<<grid, kFbThreads, 0, st>>>(m->D, A);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
 }  // namespace pic
 
 extern "C" {
@@ -630,9 +748,11 @@ int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T
     if (!(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) ||
         !(opt->eps > 0.f))
         return PIC_ERR_INVALID_ARG;
-    // a multiplier coprime with n_data: the batches walk a fixed permutation
-    long long mul = (long long)(seed % (uint64_t)n_data) | 1ll;
-    if (mul < 2) mul = n_data > 2 ? n_data / 2 + 1 : 1;
+    // a multiplier coprime with n_data near n_data times the golden ratio
+    // (shifted by the seed): consecutive batch rows land far apart in the
+    // data set, and the batches walk a fixed permutation of it
+    long long mul = (long long)((double)n_data * 0.6180339887498949) + (long long)(seed % 1024ull);
+    if (mul < 1) mul = 1;
     while (gcd_ll(mul, n_data) != 1) ++mul;
     cudaError_t e = cudaSuccess;
     for (long long s = 0; s < steps && e == cudaSuccess; ++s) {

@@ -177,6 +177,34 @@ cudaError_t launch_moments32(const DevParams& P, const WinBufs32& B, double* par
 }  // namespace pic
 
 namespace pic {
+// Learned stepper (mlp.cu): y <- y_plain + scale * net(y_prev, phase, dt) where
+// the frozen-field energy allows it.  y_prev / y are the state before and
+// after the plain step, in storage order (double2 for precision 0, float2 for 1).
+struct LearnedArgs {
+    const void* y_prev;
+    void* y;
+    long long n;
+    int prec;
+    float in_sin, in_cos, in_dt;   // the inputs shared by every particle
+    float scale_R, scale_V;        // output scaling of the network
+    double tol;                    // energy-drift limit (relative)
+    int field;                     // PIC_FIELD_*
+    double eps;
+    const double* E;               // Poisson: node field at t_n (n_cells+1)
+    const double* psi;             // potential with psi' = E, psi = 0 at r = 0
+    const double* edges;           // rE at r_min and r_max
+    double r_min, hr, inv_hr;
+    int n_cells;
+    unsigned long long* n_fallback;
+};
+cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_count, cudaStream_t st,
+                                 long long* launches);
+// psi at the nodes from E at the nodes (trapezoid of the piecewise-linear field).
+cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* psi, cudaStream_t st,
+                             long long* launches);
+}  // namespace pic
+
+namespace pic {
 // Poisson prefix integral on caller-provided scan scratch (api.cu).
 int poisson_with_scratch(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
                          double* rE_edges_dev, const ScanScratch* S, void* stream);

@@ -149,6 +149,8 @@ def load() -> C.CDLL:
             "pic_mlp_gradients": (i32, [vp, i64, vp, vp, vp, vp, i32]),
             "pic_mlp_train": (i32, [vp, i64, vp, vp, i64, i64, P(pic_adam_t), C.c_uint64, vp]),
             "pic_mlp_destroy": (None, [vp]),
+            "pic_step_learned": (i32, [H, vp, i64, C.c_float, C.c_float, d, P(i64)]),
+            "pic_fine_advance": (i32, [H, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -415,3 +417,16 @@ def pic_mlp_train(m: Mlp, X_dev, T_dev, batch: int, steps: int, lr=1e-3, beta1=0
     _check(load().pic_mlp_train(m.ptr, int(X_dev.shape[0]), _ptr(X_dev)[0], _ptr(T_dev)[0], int(batch), int(steps),
                                 C.byref(opt), C.c_uint64(seed), hist.ctypes.data), "pic_mlp_train")
     return hist[:int(steps)]
+
+
+def pic_step_learned(h: Handle, m: Mlp, n_steps: int, scale=(1.0, 1.0), drift_tol: float = 1e-4) -> int:
+    """Learned-stepper macro steps; returns the number of particle-steps that fell back to the plain step."""
+    nfb = C.c_int64(0)
+    _check(load().pic_step_learned(h.ptr, m.ptr, int(n_steps), float(scale[0]), float(scale[1]), float(drift_tol),
+                                   C.byref(nfb)), "pic_step_learned")
+    return int(nfb.value)
+
+
+def pic_fine_advance(h: Handle, t: float) -> None:
+    """The reference solution over time t: fine steps of h and one last partial step."""
+    _check(load().pic_fine_advance(h.ptr, float(t)), "pic_fine_advance")
