@@ -48,6 +48,12 @@ WORKLOADS = {
     # Duffing test field, periods once at init
     "duffing1e4": dict(n=10**4, params=dict(field_model=1, dt=0.05, periods_once=1), r_cut=None,
                        desc="Duffing E=-r^3, eps=0.01, N_p=1e4, dt=0.05, periods once, FP64"),
+    # learned stepper: network-corrected improved-ETD steps of dt = 0.4 (FP32 form underneath)
+    "learned1e7": dict(n=10**7, params=dict(precision=1, dt=0.4, n_cells=512, sort_every=4), r_cut=4.0,
+                       learned=dict(train_n=100_000, train_macro=3, steps=1500, batch=8192, tol=1e-4, eval_n=20_000),
+                       desc="Learned stepper: Vlasov-Poisson, eps=0.01, N_p=1e7, N_r=512 on [-4,4], CIC, dt=0.4, "
+                            "improved-ETD step (FP32 form) + 5-64-64-2 GELU network (BF16 weights, FP32 accumulate), "
+                            "frozen-field energy check 1e-4"),
     # FP32 form of the same physics at eps = 1e-3 (N about 15 periods per step)
     "vp1e8_f32": dict(n=10**8, params=dict(precision=1, eps=1e-3, n_cells=1024, max_window_steps=202, sort_every=4),
                       r_cut=4.0, error_n=10**6, error_steps=20,
@@ -184,11 +190,33 @@ def run_ours(args):
     R0, V0 = inputs.gaussian_beam(n, seed=rank, r_cut=wl["r_cut"])
     prm = make_params(pic, args.workload)
     stream = torch.cuda.current_stream()
+    lw = wl.get("learned")
+    net = None
+    learned_info = None
+    if lw:
+        # train the correction network before anything is timed
+        from paper_1404_1160_gb300 import learned as _learned
+
+        t_tr = time.perf_counter()
+        beam = inputs.gaussian_beam(lw["train_n"], seed=100 + rank, r_cut=wl["r_cut"])
+        X, T = _learned.make_dataset(prm, [beam], n_macro=lw["train_macro"], reference="fine")
+        net, out_scale, hist, kept = _learned.train(X, T, steps=lw["steps"], batch=lw["batch"], seed=1)
+        learned_info = {"train_samples": int(X.shape[0]), "train_steps": lw["steps"], "kept": kept,
+                        "loss_first": float(np.mean(hist[:10])), "loss_last": float(np.mean(hist[-50:])),
+                        "train_s": time.perf_counter() - t_tr}
     h = pic.pic_init(prm, torch.from_numpy(R0).cuda(), torch.from_numpy(V0).cuda(), stream)
+    n_fb = [0]
+
+    def do_step():
+        if net is None:
+            pic.pic_step(h, 1)
+        else:
+            n_fb[0] += pic.pic_step_learned(h, net, 1, scale=tuple(out_scale), drift_tol=lw["tol"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     for _ in range(args.warmup):
-        pic.pic_step(h, 1)
+        do_step()
     torch.cuda.synchronize()
+    n_fb[0] = 0
     if world > 1:
         dist.barrier()
     launches0 = pic.pic_launch_count(h)
@@ -200,7 +228,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
             evs[k][0].record(stream)
-            pic.pic_step(h, 1)
+            do_step()
             evs[k][1].record(stream)
             win_ms.append(pic.pic_window_time(h)[0])  # window kernel, timed by the library on this stream
         torch.cuda.synchronize()
@@ -227,7 +255,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         pic.pic_set_particles(h, r_h, v_h)
-        pic.pic_step(h, 1)
+        do_step()
         pic.pic_get_particles(h, r_o, v_o)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -281,11 +309,58 @@ def run_ours(args):
     }
     if f32 and "error_n" in wl:
         line["error_vs_fp64"] = error_vs_fp64(args.workload)
+    if lw:
+        learned_info["fallback_fraction"] = n_fb[0] / float(n * args.steps)
+        learned_info.update(learned_errors(prm, wl, net, out_scale))
+        line["learned"] = learned_info
+        net.close()
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def learned_errors(prm, wl, net, out_scale):
+    """Errors after one macro step of dt, on a held-out sample of the same
+    beam, against the reference solution (fine solver over dt on the FP64
+    path, bit-identical to the oracle's brute force): the plain large step,
+    the learned step, and 8 plain steps of dt/8."""
+    import ctypes
+
+    from paper_1404_1160_gb300 import inputs
+    from paper_1404_1160_gb300 import pic
+
+    lw = wl["learned"]
+    R0, V0 = inputs.gaussian_beam(lw["eval_n"], seed=999, r_cut=wl["r_cut"])
+
+    def clone(**kw):
+        p = pic.pic_params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(prm), ctypes.sizeof(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    out = {}
+    ref = pic.pic_init(clone(precision=0), R0, V0)
+    pic.pic_fine_advance(ref, prm.dt)
+    Rf, Vf = pic.pic_get_particles(ref)
+    pic.pic_destroy(ref)
+    for name, p, how in (("plain", prm, "plain"), ("learned", prm, "learned"), ("plain_8_small", clone(dt=prm.dt / 8), "8")):
+        h = pic.pic_init(p, R0, V0)
+        if how == "plain":
+            pic.pic_step(h, 1)
+        elif how == "learned":
+            pic.pic_step_learned(h, net, 1, scale=tuple(out_scale), drift_tol=lw["tol"])
+        else:
+            pic.pic_step(h, 8)
+        R, V = pic.pic_get_particles(h)
+        pic.pic_destroy(h)
+        e = np.sort(np.hypot(R - Rf, V - Vf))
+        out[f"err_{name}_median"] = float(np.median(e))
+        out[f"err_{name}_rms99"] = float(np.sqrt(np.mean(e[:int(0.99 * e.size)] ** 2)))
+    out["error_sample"] = f"{lw['eval_n']} held-out particles of the same beam, one macro step, vs the fine-solver reference"
+    return out
 
 
 def measured_hbm_peak() -> float:
@@ -355,8 +430,9 @@ def cpu_baseline(workload: str, n_sample: int):
         el = time.perf_counter() - t0
         if el > 8.0 or steps >= 1000:
             break
+    note = " (the plain improved-ETD step: the oracle has no network)" if wl.get("learned") else ""
     return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} macro step(s) of {n} particles of the same workload ({el:.1f} s)"}
+            "sample": f"{steps} macro step(s) of {n} particles of the same workload ({el:.1f} s){note}"}
 
 
 def cfg_periods_once(workload):
