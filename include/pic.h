@@ -316,6 +316,44 @@ void pic_mlp_destroy(pic_mlp* m);
 int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float scale_R, float scale_V,
                      double drift_tol, int64_t* n_fallback);
 
+/* ---- batched form ------------------------------------------------------- */
+/* Many independent beams (each its own pic_params: eps, dt, mesh, field
+   model; FP32 form, precision = 1) advanced together: one cooperative
+   launch per macro step serves every beam, each on a share of the GPU's
+   blocks (in proportion to its particles^alloc_power; a quarter weight for
+   the analytic fields), with barriers among its own blocks only.  The step
+   (reset, launch, status gather) is replayed from a captured CUDA graph,
+   captured again after a phase-space sort has moved buffers.  A beam's
+   results do not depend on the launch shape, the block share or the sort
+   period: every beam computes bit for bit what pic_step computes for it
+   alone.  Beam arrays are host memory. */
+typedef struct pic_batch pic_batch;
+typedef struct {
+    int32_t block, blocks_per_sm, grid, sort_every, graph;
+    int32_t pad_;
+    double  alloc_power;
+} pic_batch_config_t;
+
+int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n_particles,
+                     const double* const* r0, const double* const* v0, void* stream, pic_batch** out);
+/* n_steps macro steps of every beam.  Synchronises after each step and
+   returns the first non-OK device status of any beam. */
+int pic_batch_step(pic_batch* b, int64_t n_steps);
+int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power,
+                         int32_t sort_every);
+int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
+/* Autotuner: times steps_per_trial macro steps (after one warm step) for
+   each launch shape (block size x blocks per SM x allocation power) that
+   fits, keeps the fastest, then times the sort periods 1, 4, 16 and keeps
+   the fastest.  The trial steps are real steps of the batch (their results
+   do not depend on the shape).  *best receives the chosen configuration. */
+int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);
+int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind);
+int pic_batch_moments(pic_batch* b, int32_t beam, pic_moments_t* out);
+int64_t pic_batch_steps(const pic_batch* b);
+int64_t pic_batch_launch_count(const pic_batch* b);
+void pic_batch_destroy(pic_batch* b);
+
 /* ---- testing ------------------------------------------------------------ */
 /* Runs one macro step of a small Poisson beam (in the given precision, 0 or
    1) whose grid barrier waits for one more arrival than the grid has, so

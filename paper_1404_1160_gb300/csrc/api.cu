@@ -1114,3 +1114,334 @@ int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* str
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batched form
+
+struct pic_batch {
+    std::vector<pic_handle*> hs;
+    cudaStream_t st = nullptr;
+    int sm_count = 0;
+    int n = 0;
+    pic::BeamDesc32* d_desc = nullptr;
+    int* d_status = nullptr;
+    int* h_status = nullptr;  // pinned
+    std::vector<pic::BeamDesc32> desc;
+    int block = 1024, bps = 1, grid = 0, sort_every = 4;
+    double alloc_power = 1.0;
+    size_t smem = 0;
+    int max_cells = 0;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = false, use_graph = true;
+    long long steps = 0, launches = 0;
+};
+
+namespace {
+
+void batch_drop_graph(pic_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_ok = false;
+}
+
+// Descriptors of the current buffers (the sort swaps them) and launch shape.
+cudaError_t batch_upload(pic_batch* b) {
+    for (int i = 0; i < b->n; ++i) {
+        pic_handle* h = b->hs[i];
+        pic::BeamDesc32& d = b->desc[i];
+        d.P = h->dp;
+        d.B = h->B32;
+        d.Tin = h->prm.periods_once ? h->Tin32 : nullptr;
+        d.T_known = h->prm.periods_once ? 1 : 0;
+        d.coop = h->prm.field_model == PIC_FIELD_POISSON ? 1 : 0;
+    }
+    batch_drop_graph(b);
+    return cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(pic::BeamDesc32) * b->n, cudaMemcpyHostToDevice, b->st);
+}
+
+// Blocks per beam in proportion to (its particles)^power, at least one and
+// at most what its particles fill; weight 1/4 for the analytic fields (no
+// field cycle).
+int batch_configure(pic_batch* b, int block, int bps_want, double power) {
+    if (block < 128 || block > 1024 || (block & 31)) return PIC_ERR_INVALID_ARG;
+    if (b->smem > 0) {
+        cudaError_t e = pic::window32_batch_attr(b->smem);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    int bps = 0;
+    cudaError_t e = pic::window32_batch_occupancy(block, b->smem, &bps);
+    if (e != cudaSuccess) return map_cuda(e);
+    if (bps < 1) return PIC_ERR_UNSUPPORTED;
+    if (bps_want > 0 && bps_want < bps) bps = bps_want;
+    const long long G = (long long)bps * b->sm_count;
+    if (G < b->n) return PIC_ERR_UNSUPPORTED;
+    std::vector<double> w(b->n);
+    std::vector<long long> need(b->n), nb(b->n);
+    double wsum = 0.0;
+    for (int i = 0; i < b->n; ++i) {
+        pic_handle* h = b->hs[i];
+        const bool coop = h->prm.field_model == PIC_FIELD_POISSON;
+        const long long groups = (h->B32.ld + 127) / 128;
+        need[i] = coop ? (groups + block / 32 - 1) / (block / 32) : (h->n + block - 1) / block;
+        if (need[i] < 1) need[i] = 1;
+        w[i] = (coop ? 1.0 : 0.25) * std::pow((double)(h->n > 0 ? h->n : 1), power);
+        wsum += w[i];
+    }
+    long long used = 0;
+    for (int i = 0; i < b->n; ++i) {
+        long long k = (long long)std::floor((double)(G - b->n) * w[i] / wsum) + 1;
+        nb[i] = k < need[i] ? k : need[i];
+        used += nb[i];
+    }
+    // hand out what is left, largest deficit first
+    while (used < G) {
+        int best = -1;
+        double bestd = 0.0;
+        for (int i = 0; i < b->n; ++i) {
+            if (nb[i] >= need[i]) continue;
+            const double d = (double)G * w[i] / wsum - (double)nb[i];
+            if (best < 0 || d > bestd) {
+                best = i;
+                bestd = d;
+            }
+        }
+        if (best < 0) break;
+        ++nb[best];
+        ++used;
+    }
+    int first = 0;
+    for (int i = 0; i < b->n; ++i) {
+        pic_handle* h = b->hs[i];
+        if (h->prm.field_model == PIC_FIELD_POISSON) {
+            const long long groups = (h->B32.ld + 127) / 128;
+            if ((groups + nb[i] - 1) / nb[i] * 128 > (1ll << 21)) return PIC_ERR_UNSUPPORTED;
+        }
+        b->desc[i].first_block = first;
+        b->desc[i].n_blocks = (int)nb[i];
+        first += (int)nb[i];
+    }
+    b->grid = first;
+    b->block = block;
+    b->bps = bps;
+    b->alloc_power = power;
+    return map_cuda(batch_upload(b));
+}
+
+cudaError_t batch_enqueue_step(pic_batch* b) {
+    cudaError_t e = pic::launch_batch_reset(b->d_desc, b->n, b->st);
+    if (e == cudaSuccess) e = pic::launch_window32_batch(b->d_desc, b->n, b->grid, b->block, b->smem, b->st);
+    if (e == cudaSuccess) e = pic::launch_batch_status(b->d_desc, b->n, b->d_status, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->st);
+    return e;
+}
+
+// One macro step of every beam: sorts when due, then the captured graph of
+// reset + cooperative window + status gather (captured again after a sort
+// has moved buffers).
+int batch_one_step(pic_batch* b) {
+    cudaError_t e = cudaSuccess;
+    if (b->sort_every > 0 && b->steps % b->sort_every == 0) {
+        for (int i = 0; i < b->n && e == cudaSuccess; ++i)
+            if (b->hs[i]->n > 0) e = pic::launch_phase_sort32(b->hs[i]->sort32, b->hs[i]->n, b->sm_count, b->st, &b->launches);
+        if (e == cudaSuccess) e = batch_upload(b);
+    }
+    if (e == cudaSuccess && b->use_graph && !b->graph_ok) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t e1 = batch_enqueue_step(b);
+            const cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+            b->graph_ok = true;
+        } else {
+            // stream capture of this launch is not available: launch directly
+            cudaGetLastError();
+            b->use_graph = false;
+            e = cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = b->use_graph ? cudaGraphLaunch(b->exec, b->st) : batch_enqueue_step(b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return map_cuda(e);
+    b->launches += 3;
+    for (int i = 0; i < b->n; ++i)
+        if (b->h_status[i] != pic::DEV_OK) return map_dev(b->h_status[i]);
+    for (pic_handle* h : b->hs) {
+        h->t += h->prm.dt;
+        h->n_steps += 1;
+        h->have_periods = 1;
+    }
+    b->steps += 1;
+    return PIC_OK;
+}
+
+void batch_free(pic_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    batch_drop_graph(b);
+    for (pic_handle* h : b->hs) pic_destroy(h);
+    b->hs.clear();
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_status) cudaFree(b->d_status);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n_particles, const double* const* r0,
+                     const double* const* v0, void* stream, pic_batch** out) {
+    if (!out || n_beams < 1 || n_beams > 4096 || !params || !n_particles || !r0 || !v0) return PIC_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_beams; ++i) {
+        if (params[i].precision != 1) return PIC_ERR_UNSUPPORTED;
+        if (params[i].field_model == PIC_FIELD_POISSON && params[i].n_cells > pic::kMaxCellsWindow)
+            return PIC_ERR_UNSUPPORTED;
+    }
+    int sms = 0;
+    int rc = current_sm_count(&sms);
+    if (rc) return rc;
+    pic_batch* b = new (std::nothrow) pic_batch();
+    if (!b) return PIC_ERR_NO_MEMORY;
+    b->st = (cudaStream_t)stream;
+    b->sm_count = sms;
+    b->n = n_beams;
+    b->desc.resize(n_beams);
+    std::memset(b->desc.data(), 0, sizeof(pic::BeamDesc32) * n_beams);
+    for (int i = 0; i < n_beams && !rc; ++i) {
+        pic_params p = params[i];
+        p.sort_every = 1;  // sort buffers exist; the batch decides when to sort
+        pic_handle* h = nullptr;
+        rc = pic_init(&p, n_particles[i], r0[i], v0[i], PIC_PTR_HOST, stream, &h);
+        if (!rc) {
+            b->hs.push_back(h);
+            if (p.field_model == PIC_FIELD_POISSON && p.n_cells > b->max_cells) b->max_cells = p.n_cells;
+        }
+    }
+    if (!rc) {
+        b->smem = pic::window32_batch_smem(b->max_cells);
+        cudaError_t e = cudaMalloc(&b->d_desc, sizeof(pic::BeamDesc32) * n_beams);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * n_beams);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * n_beams);
+        rc = map_cuda(e);
+    }
+    if (!rc) rc = batch_configure(b, 1024, 1, 1.0);
+    if (!rc) rc = map_cuda(cudaStreamSynchronize(b->st));
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+int pic_batch_step(pic_batch* b, int64_t n_steps) {
+    if (!b || n_steps < 0) return PIC_ERR_INVALID_ARG;
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const int rc = batch_one_step(b);
+        if (rc) return rc;
+    }
+    return PIC_OK;
+}
+
+int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power, int32_t sort_every) {
+    if (!b || sort_every < 0 || !(alloc_power >= 0.0 && alloc_power <= 2.0)) return PIC_ERR_INVALID_ARG;
+    const int rc = batch_configure(b, block, blocks_per_sm, alloc_power);
+    if (!rc) b->sort_every = sort_every;
+    return rc;
+}
+
+int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out) {
+    if (!b || !out) return PIC_ERR_INVALID_ARG;
+    out->block = b->block;
+    out->blocks_per_sm = b->bps;
+    out->grid = b->grid;
+    out->sort_every = b->sort_every;
+    out->alloc_power = b->alloc_power;
+    out->graph = b->use_graph ? 1 : 0;
+    return PIC_OK;
+}
+
+int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best) {
+    if (!b || steps_per_trial < 1) return PIC_ERR_INVALID_ARG;
+    struct Cand {
+        int block, bps;
+        double power;
+    };
+    const Cand shapes[] = {{1024, 1, 1.0}, {1024, 1, 0.85}, {512, 2, 1.0}, {512, 2, 0.85}, {256, 4, 1.0}};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIC_ERR_CUDA;
+    auto trial = [&](double* ms) -> int {
+        int rc = batch_one_step(b);  // capture and warm
+        if (rc) return rc;
+        cudaEventRecord(e0, b->st);
+        for (int s = 0; s < steps_per_trial && !rc; ++s) rc = batch_one_step(b);
+        cudaEventRecord(e1, b->st);
+        cudaEventSynchronize(e1);
+        float x = 0.f;
+        cudaEventElapsedTime(&x, e0, e1);
+        *ms = (double)x / steps_per_trial;
+        return rc;
+    };
+    double best_ms = 1e300;
+    Cand bestc = shapes[0];
+    int rc = PIC_OK;
+    for (const Cand& c : shapes) {
+        int r = batch_configure(b, c.block, c.bps, c.power);
+        if (r == PIC_ERR_UNSUPPORTED) continue;  // shape does not fit this batch
+        if (r) {
+            rc = r;
+            break;
+        }
+        double ms = 0.0;
+        if ((rc = trial(&ms))) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            bestc = c;
+        }
+    }
+    if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power);
+    int best_sort = b->sort_every;
+    if (!rc) {
+        double best_sort_ms = 1e300;
+        const int sorts[] = {1, 4, 16};
+        for (int so : sorts) {
+            b->sort_every = so;
+            double ms = 0.0;
+            if ((rc = trial(&ms))) break;
+            if (ms < best_sort_ms) {
+                best_sort_ms = ms;
+                best_sort = so;
+            }
+        }
+        b->sort_every = best_sort;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return pic_batch_get_config(b, best);
+}
+
+int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind) {
+    if (!b || beam < 0 || beam >= b->n) return PIC_ERR_INVALID_ARG;
+    return pic_get_particles(b->hs[beam], r, v, ptr_kind);
+}
+
+int pic_batch_moments(pic_batch* b, int32_t beam, pic_moments_t* out) {
+    if (!b || beam < 0 || beam >= b->n) return PIC_ERR_INVALID_ARG;
+    return pic_moments(b->hs[beam], out);
+}
+
+int64_t pic_batch_steps(const pic_batch* b) { return b ? b->steps : -1; }
+
+int64_t pic_batch_launch_count(const pic_batch* b) { return b ? b->launches : -1; }
+
+void pic_batch_destroy(pic_batch* b) { batch_free(b); }
+
+}  // extern "C"

@@ -113,6 +113,26 @@ cudaError_t launch_window32_coop(const DevParams& P, const WinBufs32& B, const W
                                  const CTime* Tin);
 cudaError_t launch_window32_local(const DevParams& P, const WinBufs32& B, int mode, int T_known, long long n_iter,
                                   int block, int sm_count, cudaStream_t st, long long* launches, const CTime* Tin);
+// Batched form: many FP32 beams in one cooperative launch.  Block b serves
+// the beam whose range [first_block, first_block + n_blocks) holds b.
+struct BeamDesc32 {
+    DevParams P;
+    WinBufs32 B;
+    const CTime* Tin;     // periods kept from initialisation (periods_once), or null
+    int first_block, n_blocks;
+    int coop;             // 1: Poisson (cooperative window), 0: analytic field (per particle)
+    int T_known;
+};
+size_t window32_batch_smem(int max_cells);
+cudaError_t window32_batch_attr(size_t smem);
+cudaError_t window32_batch_occupancy(int block, size_t smem, int* blocks_per_sm);
+cudaError_t launch_window32_batch(const BeamDesc32* beams, int n_beams, int grid, int block, size_t smem,
+                                  cudaStream_t st);
+// Clears every beam's charge ring, barrier, counters and status (one launch).
+cudaError_t launch_batch_reset(const BeamDesc32* beams, int n_beams, cudaStream_t st);
+// Copies every beam's status word into out[n_beams].
+cudaError_t launch_batch_status(const BeamDesc32* beams, int n_beams, int* out, cudaStream_t st);
+
 // Binary32 deposit (the FP32 form's quantisation), R read as R[i * r_stride].
 cudaError_t launch_deposit32(const DevParams& P, const float* R, long long n, int r_stride, long long* Q,
                              long long* n_out, cudaStream_t st, int sm_count, long long* launches);

@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         flush_hist<HIST>(P, B, hist, cyc);
         if (blockIdx.x == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
         if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
-        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok, gridDim.x)) return;
         if (!fine_only) {
             if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
             __syncthreads();
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         if (STAGE) cp_async_wait<0>();
         __syncthreads();
         flush_hist<HIST>(P, B, hist, cyc);
-        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok, gridDim.x)) return;
         build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
         ++cyc;
     }

@@ -70,7 +70,8 @@ __device__ __forceinline__ unsigned long long hist32_node(const unsigned int* h,
 
 // Adds this block's two histograms to the cycle's global charge; block 0
 // clears the charge of the cycle after.
-__device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, const unsigned int* hist, int cyc) {
+__device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, const unsigned int* hist, int cyc,
+                                        int lb) {
     const int Np1 = P.n_cells + 1;
     unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad;
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
@@ -78,7 +79,7 @@ __device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, 
         const unsigned long long v = hist32_node(hist + f * kHist32Words * Np1, Np1, j, P.W);
         if (v) atomicAdd(Qg + (size_t)idx * kQPad, v);
     }
-    if (blockIdx.x == 0) {
+    if (lb == 0) {
         unsigned long long* Qn = B.Qring + (size_t)((cyc + 1) % 3) * 2 * Np1 * kQPad;
         for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) Qn[(size_t)idx * kQPad] = 0ull;
     }
@@ -257,9 +258,11 @@ static size_t coop32_smem_bytes(int n_cells) {
            + 4 * Np1 * sizeof(float2);                    // tables of pair 1 and pair 2
 }
 
-__global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, WinBufs32 B, int mode, int T_known,
-                                                                  long long n_fine, const CTime* __restrict__ Tin) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// The window of one beam on blocks lb = 0..nb-1 of its own (the whole grid
+// for a single beam, or a beam's share of a batch).
+__device__ __forceinline__ void window32_coop_body(const DevParams& P, const WinBufs32& B, int mode, int T_known,
+                                                   long long n_fine, const CTime* __restrict__ Tin, int lb, int nb,
+                                                   unsigned char* smem_raw) {
     const int Nc = P.n_cells, Np1 = Nc + 1;
     const int hw = kHist32Words * Np1;
     unsigned int* hist = (unsigned int*)smem_raw;  // 2 fields x hw words
@@ -283,8 +286,7 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
     // the next so that the first groups a sweep reads are the last ones the
     // previous sweep touched (still in L2).
     const long long n_groups = ld / kGroup;
-    const long long my_groups =
-        (long long)blockIdx.x < n_groups ? (n_groups - 1 - (long long)blockIdx.x) / gridDim.x + 1 : 0;
+    const long long my_groups = (long long)lb < n_groups ? (n_groups - 1 - (long long)lb) / nb + 1 : 0;
     bool rev = false;
     auto grab = [&]() -> long long {
         int m = 0;
@@ -292,14 +294,14 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
         m = __shfl_sync(0xffffffffu, m, 0);
         if (m >= my_groups) return -1;
         const long long mm = rev ? my_groups - 1 - m : m;
-        return (long long)blockIdx.x + mm * gridDim.x;
+        return (long long)lb + mm * nb;
     };
     auto row = [&](long long k) -> float2* {
         if (fine_only) return (k & 1) ? B.traj : B.y;
         return k == 0 ? B.y : B.traj + (size_t)(k - 1) * ld;
     };
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)lb * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)nb * blockDim.x;
 
     if (!fine_only) {
         for (long long i = tid; i < n; i += nthreads) {
@@ -401,10 +403,10 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
             if (lane == 0 && cnt) atomicAdd(&s_cnt, (int)cnt);
         }
         __syncthreads();
-        flush32(P, B, hist, cyc);
-        if (blockIdx.x == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
+        flush32(P, B, hist, cyc, lb);
+        if (lb == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
         if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
-        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok, (unsigned int)nb)) return;
         if (track) {
             if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
             __syncthreads();
@@ -451,14 +453,14 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
         }
         rev = !rev;
         __syncthreads();
-        flush32(P, B, hist, cyc);
-        if (!grid_sync(P, B.bar, gen, B.status, &s_ok)) return;
+        flush32(P, B, hist, cyc, lb);
+        if (!grid_sync(P, B.bar, gen, B.status, &s_ok, (unsigned int)nb)) return;
         build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabB, inv_r, s_edB,
                        s_warp, s_c);
         ++cyc;
     }
 
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !fine_only) *B.K_out = K;
+    if (lb == 0 && threadIdx.x == 0 && !fine_only) *B.K_out = K;
     if (mode != MODE_ETD) return;
 
     // ---- landing (step 3) and extrapolation (step 4); row k holds z_k
@@ -491,6 +493,12 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
     }
 }
 
+__global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, WinBufs32 B, int mode, int T_known,
+                                                                  long long n_fine, const CTime* __restrict__ Tin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    window32_coop_body(P, B, mode, T_known, n_fine, Tin, blockIdx.x, gridDim.x, smem_raw);
+}
+
 // ------------------------------------------- per-particle window (analytic E)
 
 // One fine step k -> k+1 of Lawson RK4 in the rotating frame, analytic field.
@@ -513,12 +521,12 @@ __device__ __forceinline__ float2 y_of(const DevParams& P, long long k, float zR
 }
 
 template <int FIELD>
-__global__ void __launch_bounds__(256) k_window32_local(DevParams P, WinBufs32 B, int mode, int T_known,
-                                                        long long n_iter, const CTime* __restrict__ Tin) {
+__device__ __forceinline__ void window32_local_body(const DevParams& P, const WinBufs32& B, int mode, int T_known,
+                                                    long long n_iter, const CTime* __restrict__ Tin, int lb, int nb) {
     const long long n = P.n, ld = B.ld;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long stride = (long long)nb * blockDim.x;
     int Kmax_seen = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (long long i = (long long)lb * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float2 y0 = B.y[i];
         float zR = y0.x, zV = y0.y;
         if (mode == MODE_FINE) {
@@ -685,6 +693,100 @@ __global__ void __launch_bounds__(256) k_window32_local(DevParams P, WinBufs32 B
     }
     Kmax_seen = __reduce_max_sync(0xffffffffu, (unsigned)Kmax_seen);
     if ((threadIdx.x & 31) == 0 && Kmax_seen > 0) atomicMax((long long*)B.K_out, (long long)Kmax_seen);
+}
+
+template <int FIELD>
+__global__ void __launch_bounds__(256) k_window32_local(DevParams P, WinBufs32 B, int mode, int T_known,
+                                                        long long n_iter, const CTime* __restrict__ Tin) {
+    window32_local_body<FIELD>(P, B, mode, T_known, n_iter, Tin, blockIdx.x, gridDim.x);
+}
+
+// ------------------------------------------------------------- batched form
+
+// One cooperative launch advances every beam of a batch by one macro step:
+// each block finds its beam, copies the beam's descriptor to shared memory
+// and runs that beam's window on the beam's own blocks (its barriers count
+// only them).  Beams never wait for each other.
+__global__ void __launch_bounds__(kW32Threads, 1) k_window32_batch(const BeamDesc32* __restrict__ beams, int n_beams) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BeamDesc32 D;
+    __shared__ int s_beam;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_beams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (beams[mid].first_block <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_beam = lo;
+    }
+    __syncthreads();
+    {
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(beams + s_beam);
+        unsigned int* dst = reinterpret_cast<unsigned int*>(&D);
+        for (int i = threadIdx.x; i < (int)(sizeof(BeamDesc32) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int lb = (int)blockIdx.x - D.first_block;
+    if (D.coop) window32_coop_body(D.P, D.B, MODE_ETD, D.T_known, 0, D.Tin, lb, D.n_blocks, smem_raw);
+    else if (D.P.field == 1) window32_local_body<1>(D.P, D.B, MODE_ETD, D.T_known, 1, D.Tin, lb, D.n_blocks);
+    else window32_local_body<2>(D.P, D.B, MODE_ETD, D.T_known, 1, D.Tin, lb, D.n_blocks);
+}
+
+__global__ void k_batch_reset(const BeamDesc32* __restrict__ beams, int n_beams) {
+    const int b = blockIdx.x;
+    if (b >= n_beams) return;
+    const BeamDesc32& D = beams[b];
+    if (D.coop) {
+        const size_t q = (size_t)3 * 2 * (D.P.n_cells + 1) * kQPad;
+        for (size_t i = threadIdx.x; i < q; i += blockDim.x) D.B.Qring[i] = 0ull;
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) D.B.bar[i] = 0u;
+        if (threadIdx.x < 3) D.B.notdone[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        *D.B.K_out = 0;
+        *D.B.status = 0;
+    }
+}
+
+__global__ void k_batch_status(const BeamDesc32* __restrict__ beams, int n_beams, int* __restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_beams; b += gridDim.x * blockDim.x)
+        out[b] = *beams[b].B.status;
+}
+
+size_t window32_batch_smem(int max_cells) { return max_cells > 0 ? coop32_smem_bytes(max_cells) : 0; }
+
+cudaError_t window32_batch_attr(size_t smem) {
+    return cudaFuncSetAttribute(k_window32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t window32_batch_occupancy(int block, size_t smem, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_window32_batch, block, smem);
+}
+
+cudaError_t launch_window32_batch(const BeamDesc32* beams, int n_beams, int grid, int block, size_t smem,
+                                  cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_window32_batch, beams, n_beams);
+}
+
+cudaError_t launch_batch_reset(const BeamDesc32* beams, int n_beams, cudaStream_t st) {
+    k_batch_reset<<<n_beams, 256, 0, st>>>(beams, n_beams);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_status(const BeamDesc32* beams, int n_beams, int* out, cudaStream_t st) {
+    k_batch_status<<<1, 256, 0, st>>>(beams, n_beams, out);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- moments

@@ -61,15 +61,17 @@ static __device__ void block_exscan_pairs2(const long long* q, long long* g, int
     __syncthreads();
 }
 
-// Grid barrier with a time limit; false if any block timed out or failed.
+// Barrier of the n_blocks blocks that share `bar` (the whole grid, or the
+// blocks of one beam of a batch), with a time limit; false if any block
+// timed out or failed.
 // Arrivals count on bar[0]; the last block of a generation publishes the
 // generation number in bar[32] (another cache line), which the others poll.
 static __device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& gen,
-                                          int* status, int* s_ok) {
+                                          int* status, int* s_ok, unsigned int n_blocks) {
     __syncthreads();
     ++gen;
     if (threadIdx.x == 0) {
-        const unsigned int target = gen * (gridDim.x + P.bar_extra);
+        const unsigned int target = gen * (n_blocks + P.bar_extra);
         __threadfence();
         const unsigned int old = atomicAdd(bar, 1u);
         int ok = 1;

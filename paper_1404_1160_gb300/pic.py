@@ -42,6 +42,11 @@ class pic_adam_t(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class pic_batch_config_t(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grid", C.c_int32), ("sort_every", C.c_int32),
+                ("graph", C.c_int32), ("pad_", C.c_int32), ("alloc_power", C.c_double)]
+
+
 class pic_params(C.Structure):
     _fields_ = [
         ("eps", C.c_double),
@@ -151,6 +156,16 @@ def load() -> C.CDLL:
             "pic_mlp_destroy": (None, [vp]),
             "pic_step_learned": (i32, [H, vp, i64, C.c_float, C.c_float, d, P(i64)]),
             "pic_fine_advance": (i32, [H, d]),
+            "pic_batch_create": (i32, [i32, P(pic_params), P(i64), P(C.c_void_p), P(C.c_void_p), vp, P(vp)]),
+            "pic_batch_step": (i32, [vp, i64]),
+            "pic_batch_set_config": (i32, [vp, i32, i32, d, i32]),
+            "pic_batch_get_config": (i32, [vp, P(pic_batch_config_t)]),
+            "pic_batch_tune": (i32, [vp, i32, P(pic_batch_config_t)]),
+            "pic_batch_get_particles": (i32, [vp, i32, vp, vp, i32]),
+            "pic_batch_moments": (i32, [vp, i32, P(pic_moments_t)]),
+            "pic_batch_steps": (i64, [vp]),
+            "pic_batch_launch_count": (i64, [vp]),
+            "pic_batch_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -430,3 +445,87 @@ def pic_step_learned(h: Handle, m: Mlp, n_steps: int, scale=(1.0, 1.0), drift_to
 def pic_fine_advance(h: Handle, t: float) -> None:
     """The reference solution over time t: fine steps of h and one last partial step."""
     _check(load().pic_fine_advance(h.ptr, float(t)), "pic_fine_advance")
+
+
+# ------------------------------------------------------------ batched form
+
+
+class Batch:
+    """Owner of a pic_batch*; pic_batch_destroy runs when it is closed or collected."""
+
+    def __init__(self, ptr: int, sizes):
+        self.ptr = C.c_void_p(ptr)
+        self.sizes = list(sizes)
+
+    def close(self):
+        if self.ptr:
+            load().pic_batch_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pic_batch_create(params_list, beams, stream=None) -> Batch:
+    """params_list: pic_params per beam; beams: (r0, v0) host arrays per beam."""
+    nb = len(params_list)
+    P = (pic_params * nb)(*params_list)
+    arrs = [(np.ascontiguousarray(r, np.float64), np.ascontiguousarray(v, np.float64)) for r, v in beams]
+    n = (C.c_int64 * nb)(*[a[0].size for a in arrs])
+    r0 = (C.c_void_p * nb)(*[a[0].ctypes.data for a in arrs])
+    v0 = (C.c_void_p * nb)(*[a[1].ctypes.data for a in arrs])
+    out = C.c_void_p()
+    _check(load().pic_batch_create(nb, P, n, r0, v0, _stream(stream), C.byref(out)), "pic_batch_create")
+    return Batch(out.value, [a[0].size for a in arrs])
+
+
+def pic_batch_step(b: Batch, n_steps: int) -> None:
+    _check(load().pic_batch_step(b.ptr, int(n_steps)), "pic_batch_step")
+
+
+def pic_batch_set_config(b: Batch, block: int, blocks_per_sm: int, alloc_power: float, sort_every: int) -> None:
+    _check(load().pic_batch_set_config(b.ptr, int(block), int(blocks_per_sm), float(alloc_power), int(sort_every)),
+           "pic_batch_set_config")
+
+
+def _cfg_dict(c) -> dict:
+    return {"block": c.block, "blocks_per_sm": c.blocks_per_sm, "grid": c.grid, "sort_every": c.sort_every,
+            "graph": c.graph, "alloc_power": c.alloc_power}
+
+
+def pic_batch_get_config(b: Batch) -> dict:
+    c = pic_batch_config_t()
+    _check(load().pic_batch_get_config(b.ptr, C.byref(c)), "pic_batch_get_config")
+    return _cfg_dict(c)
+
+
+def pic_batch_tune(b: Batch, steps_per_trial: int = 2) -> dict:
+    c = pic_batch_config_t()
+    _check(load().pic_batch_tune(b.ptr, int(steps_per_trial), C.byref(c)), "pic_batch_tune")
+    return _cfg_dict(c)
+
+
+def pic_batch_get_particles(b: Batch, beam: int):
+    n = b.sizes[beam]
+    r = np.empty(n, np.float64)
+    v = np.empty(n, np.float64)
+    _check(load().pic_batch_get_particles(b.ptr, int(beam), r.ctypes.data, v.ctypes.data, PIC_PTR_HOST),
+           "pic_batch_get_particles")
+    return r, v
+
+
+def pic_batch_moments(b: Batch, beam: int) -> dict:
+    m = pic_moments_t()
+    _check(load().pic_batch_moments(b.ptr, int(beam), C.byref(m)), "pic_batch_moments")
+    return m.as_dict()
+
+
+def pic_batch_steps(b: Batch) -> int:
+    return int(load().pic_batch_steps(b.ptr))
+
+
+def pic_batch_launch_count(b: Batch) -> int:
+    return int(load().pic_batch_launch_count(b.ptr))
