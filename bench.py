@@ -54,6 +54,14 @@ WORKLOADS = {
                        desc="Learned stepper: Vlasov-Poisson, eps=0.01, N_p=1e7, N_r=512 on [-4,4], CIC, dt=0.4, "
                             "improved-ETD step (FP32 form) + 5-64-64-2 GELU network (BF16 weights, FP32 accumulate), "
                             "frozen-field energy check 1e-4"),
+    # batched form: 64 independent beams in one launch per macro step
+    "batch64": dict(n=0, params=dict(precision=1), r_cut=4.0,
+                    batch=dict(n_beams=64, seed=3, log_n=(4.0, 6.0), eps=(0.1, 0.05, 0.01, 0.005, 0.001),
+                               cells=(128, 256, 512, 1024), p_poisson=0.75, dt=0.1),
+                    desc="Batched form: 64 independent beams, N_p log-uniform in [1e4, 1e6], eps in "
+                         "{0.1, 0.05, 0.01, 0.005, 0.001}, N_r in {128, 256, 512, 1024} on [-4, 4], Poisson (3/4) and "
+                         "Duffing (periods once) fields, dt = 0.1, FP32 form, one cooperative graph-replayed launch "
+                         "per macro step, autotuned launch shape"),
     # FP32 form of the same physics at eps = 1e-3 (N about 15 periods per step)
     "vp1e8_f32": dict(n=10**8, params=dict(precision=1, eps=1e-3, n_cells=1024, max_window_steps=202, sort_every=4),
                       r_cut=4.0, error_n=10**6, error_steps=20,
@@ -321,6 +329,137 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batch_specs(wl):
+    """(pic_params per beam, (R0, V0) per beam) of a batched workload (seeded)."""
+    from paper_1404_1160_gb300 import inputs
+    from paper_1404_1160_gb300 import pic
+
+    bw = wl["batch"]
+    rng = np.random.default_rng(bw["seed"])
+    params, beams = [], []
+    for i in range(bw["n_beams"]):
+        n = int(round(10 ** rng.uniform(*bw["log_n"])))
+        eps = float(rng.choice(bw["eps"]))
+        cells = int(rng.choice(bw["cells"]))
+        poisson = rng.uniform() < bw["p_poisson"]
+        if poisson:
+            p = pic.pic_default_params(precision=1, eps=eps, dt=bw["dt"], n_cells=cells)
+            beams.append(inputs.gaussian_beam(n, seed=1000 + i, r_cut=4.0))
+        else:
+            p = pic.pic_default_params(precision=1, eps=eps, dt=bw["dt"], field_model=pic.PIC_FIELD_DUFFING,
+                                       periods_once=1)
+            beams.append(inputs.gaussian_beam(n, seed=1000 + i))
+        params.append(p)
+    return params, beams
+
+
+def run_batch(args):
+    import torch
+
+    from paper_1404_1160_gb300 import build as _build
+    from paper_1404_1160_gb300 import pic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    wl = WORKLOADS[args.workload]
+    params, beams = batch_specs(wl)
+    sizes = np.array([r.size for r, _ in beams])
+    n_total = int(sizes.sum())
+    stream = torch.cuda.current_stream()
+    b = pic.pic_batch_create(params, beams, stream)
+    t_tune = time.perf_counter()
+    tuned = pic.pic_batch_tune(b, steps_per_trial=2)  # real steps; they also warm up
+    t_tune = time.perf_counter() - t_tune
+    pic.pic_batch_step(b, args.warmup)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    launches0 = pic.pic_batch_launch_count(b)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            pic.pic_batch_step(b, 1)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(c) for a, c in evs]
+    dev_s = sum(step_ms) / 1e3
+    value = n_total * args.steps / dev_s
+    launches = pic.pic_batch_launch_count(b) - launches0
+    Ks = np.array([pic.pic_batch_moments(b, i)["window_steps"] for i in range(len(beams))])
+    # end to end with host buffers: every beam's (R, V) in and out each step
+    host = [(torch.from_numpy(r.copy()).pin_memory(), torch.from_numpy(v.copy()).pin_memory()) for r, v in beams]
+    outs = [(torch.empty(r.size, dtype=torch.float64).pin_memory(), torch.empty(r.size, dtype=torch.float64).pin_memory())
+            for r, _ in beams]
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, (r, v) in enumerate(host):
+            pic.pic_batch_set_particles(b, i, r, v)
+        pic.pic_batch_step(b, 1)
+        for i, (r, v) in enumerate(outs):
+            pic.pic_batch_get_particles_into(b, i, r, v)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    b.close()
+    if rank != 0:
+        return
+    mean_ms = float(np.mean(step_ms))
+    bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * float(np.sum(sizes * Ks))
+    peak = measured_hbm_peak()
+    achieved = bytes_ / (mean_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_beams": len(beams), "n_particles_total": n_total,
+                   "n_particles_min": int(sizes.min()), "n_particles_max": int(sizes.max()),
+                   "fine_steps_per_window_max": int(Ks.max()), "tuned": tuned, "tune_s": t_tune,
+                   "parallelism": "single GPU", "l2": "L2 flushed between timed steps (256 MB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_window32_batch (all beams, one cooperative launch per macro step)",
+                     "kernel_ms": mean_ms, "algorithmic_bytes_per_launch": bytes_,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"},
+        "e2e": {"value": n_total * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n_total,
+                "d2h_bytes_per_step": 16 * n_total},
+        "gpu_launches": int(launches), "wall_s": wall, "clocks": clk.summary(),
+        "error_vs_oracle": "every beam bit-identical to the FP32 form run alone (tests/test_gpu_batch.py), which is "
+                           "checked against the FP64 oracle within binary32 bounds (tests/test_gpu_f32.py)",
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(params, beams)
+    print(json.dumps(line))
+
+
+def batch_cpu_baseline(params, beams, budget_s: float = 8.0):
+    """The FP64 oracle, single-threaded, on the batch's beams in order (each
+    cut to at most 2e4 particles) until the time budget is used."""
+    import oracle
+
+    done, el, t0 = 0, 0.0, time.perf_counter()
+    used = []
+    for p, (R, V) in zip(params, beams):
+        n = min(R.size, 20_000)
+        cfg = oracle.Config(eps=p.eps, dt=p.dt, field_model=p.field_model, fine_solver=1, steps_per_turn=100,
+                            n_cells=p.n_cells, r_min=p.r_min, r_max=p.r_max, total_charge=1.0,
+                            weight_fixed=p.weight_fixed, max_window_steps=p.max_window_steps)
+        T = oracle.periods(cfg, R[:n], V[:n])[0] if p.periods_once else None
+        oracle.etd_step(cfg, R[:n], V[:n], T)
+        done += n
+        used.append(n)
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one macro step of each of the first {len(used)} beams, cut to <= 2e4 particles ({el:.1f} s)"}
+
+
 def learned_errors(prm, wl, net, out_scale):
     """Errors after one macro step of dt, on a held-out sample of the same
     beam, against the reference solution (fine solver over dt on the FP64
@@ -461,6 +600,21 @@ def run_reference(args):
 
     oracle.build()
     wl = WORKLOADS[args.workload]
+    if "batch" in wl:
+        params, beams = batch_specs(wl)
+        t0 = time.perf_counter()
+        base = None
+        for _ in range(args.warmup + args.steps):
+            base = batch_cpu_baseline(params, beams, budget_s=2.0)
+        value = base["value"]
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": (time.perf_counter() - t0) * 1e3 /
+                max(1, args.warmup + args.steps), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": {"workload": wl["desc"]},
+                "cpu_baseline": dict(base), "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                    "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
     n = min(args.cpu_sample, wl["n"])
     cfg = oracle_cfg(args.workload)
     R, V = inputs.gaussian_beam(n, seed=0, r_cut=wl["r_cut"])
@@ -499,6 +653,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif "batch" in WORKLOADS[args.workload]:
+        run_batch(args)
     else:
         run_ours(args)
 

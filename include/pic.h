@@ -329,8 +329,9 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
    alone.  Beam arrays are host memory. */
 typedef struct pic_batch pic_batch;
 typedef struct {
-    int32_t block, blocks_per_sm, grid, sort_every, graph;
-    int32_t pad_;
+    int32_t block, blocks_per_sm, grid, sort_every;
+    int32_t graph;                     /* 1: steps replay a captured CUDA graph     */
+    int32_t graph_error;               /* cudaError_t of a failed capture, else 0   */
     double  alloc_power;
 } pic_batch_config_t;
 
@@ -349,6 +350,7 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
    do not depend on the shape).  *best receives the chosen configuration. */
 int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind);
+int pic_batch_set_particles(pic_batch* b, int32_t beam, const double* r, const double* v, int ptr_kind);
 int pic_batch_moments(pic_batch* b, int32_t beam, pic_moments_t* out);
 int64_t pic_batch_steps(const pic_batch* b);
 int64_t pic_batch_launch_count(const pic_batch* b);

@@ -1132,6 +1132,12 @@ struct pic_batch {
     int max_cells = 0;
     cudaGraphExec_t exec = nullptr;
     bool graph_ok = false, use_graph = true;
+    cudaError_t graph_error = cudaSuccess;
+    // the graph is captured on and replayed from a stream of the batch's own
+    // (the caller's stream may be the legacy default stream, which cannot be
+    // captured), ordered after the caller's work by an event
+    cudaStream_t gst = nullptr;
+    cudaEvent_t ev_in = nullptr;
     long long steps = 0, launches = 0;
 };
 
@@ -1226,12 +1232,11 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power) {
     return map_cuda(batch_upload(b));
 }
 
-cudaError_t batch_enqueue_step(pic_batch* b) {
-    cudaError_t e = pic::launch_batch_reset(b->d_desc, b->n, b->st);
-    if (e == cudaSuccess) e = pic::launch_window32_batch(b->d_desc, b->n, b->grid, b->block, b->smem, b->st);
-    if (e == cudaSuccess) e = pic::launch_batch_status(b->d_desc, b->n, b->d_status, b->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->st);
+cudaError_t batch_enqueue_step(pic_batch* b, cudaStream_t st) {
+    cudaError_t e = pic::launch_batch_reset(b->d_desc, b->n, st);
+    if (e == cudaSuccess) e = pic::launch_window32_batch(b->d_desc, b->n, b->grid, b->block, b->smem, st);
+    if (e == cudaSuccess) e = pic::launch_batch_status(b->d_desc, b->n, b->d_status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->n, cudaMemcpyDeviceToHost, st);
     return e;
 }
 
@@ -1247,10 +1252,10 @@ int batch_one_step(pic_batch* b) {
     }
     if (e == cudaSuccess && b->use_graph && !b->graph_ok) {
         cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCapture(b->gst, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t e1 = batch_enqueue_step(b);
-            const cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+            const cudaError_t e1 = batch_enqueue_step(b, b->gst);
+            const cudaError_t e2 = cudaStreamEndCapture(b->gst, &g);
             e = e1 != cudaSuccess ? e1 : e2;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
@@ -1258,14 +1263,24 @@ int batch_one_step(pic_batch* b) {
         if (e == cudaSuccess) {
             b->graph_ok = true;
         } else {
-            // stream capture of this launch is not available: launch directly
+            // capture is not available here: launch the same work directly
+            b->graph_error = e;
             cudaGetLastError();
             b->use_graph = false;
             e = cudaSuccess;
         }
     }
-    if (e == cudaSuccess) e = b->use_graph ? cudaGraphLaunch(b->exec, b->st) : batch_enqueue_step(b);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e == cudaSuccess) {
+        if (b->use_graph) {
+            e = cudaEventRecord(b->ev_in, b->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->gst, b->ev_in, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->gst);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->gst);
+        } else {
+            e = batch_enqueue_step(b, b->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+        }
+    }
     if (e != cudaSuccess) return map_cuda(e);
     b->launches += 3;
     for (int i = 0; i < b->n; ++i)
@@ -1282,7 +1297,10 @@ int batch_one_step(pic_batch* b) {
 void batch_free(pic_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
+    if (b->gst) cudaStreamSynchronize(b->gst);
     batch_drop_graph(b);
+    if (b->gst) cudaStreamDestroy(b->gst);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
     for (pic_handle* h : b->hs) pic_destroy(h);
     b->hs.clear();
     if (b->d_desc) cudaFree(b->d_desc);
@@ -1329,6 +1347,8 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
         cudaError_t e = cudaMalloc(&b->d_desc, sizeof(pic::BeamDesc32) * n_beams);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * n_beams);
         if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * n_beams);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
         rc = map_cuda(e);
     }
     if (!rc) rc = batch_configure(b, 1024, 1, 1.0);
@@ -1365,6 +1385,7 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out) {
     out->sort_every = b->sort_every;
     out->alloc_power = b->alloc_power;
     out->graph = b->use_graph ? 1 : 0;
+    out->graph_error = (int32_t)b->graph_error;
     return PIC_OK;
 }
 
@@ -1431,6 +1452,11 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind) {
     if (!b || beam < 0 || beam >= b->n) return PIC_ERR_INVALID_ARG;
     return pic_get_particles(b->hs[beam], r, v, ptr_kind);
+}
+
+int pic_batch_set_particles(pic_batch* b, int32_t beam, const double* r, const double* v, int ptr_kind) {
+    if (!b || beam < 0 || beam >= b->n) return PIC_ERR_INVALID_ARG;
+    return pic_set_particles(b->hs[beam], r, v, ptr_kind);
 }
 
 int pic_batch_moments(pic_batch* b, int32_t beam, pic_moments_t* out) {

@@ -44,7 +44,7 @@ class pic_adam_t(C.Structure):
 
 class pic_batch_config_t(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grid", C.c_int32), ("sort_every", C.c_int32),
-                ("graph", C.c_int32), ("pad_", C.c_int32), ("alloc_power", C.c_double)]
+                ("graph", C.c_int32), ("graph_error", C.c_int32), ("alloc_power", C.c_double)]
 
 
 class pic_params(C.Structure):
@@ -163,6 +163,7 @@ def load() -> C.CDLL:
             "pic_batch_tune": (i32, [vp, i32, P(pic_batch_config_t)]),
             "pic_batch_get_particles": (i32, [vp, i32, vp, vp, i32]),
             "pic_batch_moments": (i32, [vp, i32, P(pic_moments_t)]),
+            "pic_batch_set_particles": (i32, [vp, i32, vp, vp, i32]),
             "pic_batch_steps": (i64, [vp]),
             "pic_batch_launch_count": (i64, [vp]),
             "pic_batch_destroy": (None, [vp]),
@@ -493,7 +494,7 @@ def pic_batch_set_config(b: Batch, block: int, blocks_per_sm: int, alloc_power: 
 
 def _cfg_dict(c) -> dict:
     return {"block": c.block, "blocks_per_sm": c.blocks_per_sm, "grid": c.grid, "sort_every": c.sort_every,
-            "graph": c.graph, "alloc_power": c.alloc_power}
+            "graph": c.graph, "graph_error": c.graph_error, "alloc_power": c.alloc_power}
 
 
 def pic_batch_get_config(b: Batch) -> dict:
@@ -515,6 +516,17 @@ def pic_batch_get_particles(b: Batch, beam: int):
     _check(load().pic_batch_get_particles(b.ptr, int(beam), r.ctypes.data, v.ctypes.data, PIC_PTR_HOST),
            "pic_batch_get_particles")
     return r, v
+
+
+def pic_batch_get_particles_into(b: Batch, beam: int, r, v) -> None:
+    """Copies beam `beam` out into preallocated arrays/tensors (host or device)."""
+    (pr, kind), (pv, _) = _ptr(r), _ptr(v)
+    _check(load().pic_batch_get_particles(b.ptr, int(beam), pr, pv, kind), "pic_batch_get_particles")
+
+
+def pic_batch_set_particles(b: Batch, beam: int, r, v) -> None:
+    (pr, kind), (pv, _) = _ptr(r), _ptr(v)
+    _check(load().pic_batch_set_particles(b.ptr, int(beam), pr, pv, kind), "pic_batch_set_particles")
 
 
 def pic_batch_moments(b: Batch, beam: int) -> dict:

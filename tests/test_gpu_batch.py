@@ -82,6 +82,7 @@ def test_batch_equals_single_beams_and_ignores_the_launch_shape():
                 assert m["Q_total"] + m["n_out_of_mesh"] * (1 << 32) == SPECS[i]["n"] * (1 << 32)
         cfg = pic.pic_batch_get_config(b)
         assert cfg["grid"] >= len(SPECS)
+        assert cfg["graph"] == 1, cfg  # steps replay a captured graph
         b.close()
 
 
