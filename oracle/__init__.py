@@ -117,6 +117,7 @@ def _load():
                 "orc_derive": (i32, [P(Params), P(Derived)]),
                 "orc_deposit": (i32, [P(Params), i64, pd, pi64, pi64]),
                 "orc_deposit_f32": (i32, [P(Params), i64, P(C.c_float), pi64, pi64]),
+                "orc_classic_step": (i32, [P(Params), i64, pd, pd, i32, pd]),
                 "orc_poisson": (i32, [P(Params), i64, pi64, pi64, pd, pd]),
                 "orc_gather": (i32, [P(Params), i64, pd, pd, pd, pd]),
                 "orc_field": (i32, [P(Params), i64, pd, pd]),
@@ -257,6 +258,15 @@ def etd_step(cfg: Config, R, V, T=None) -> StepResult:
     )
     stats = {k: getattr(st, k) for k, _ in StepStats._fields_}
     return StepResult(R, V, Tarr, N, o, stats)
+
+
+def classic_step(cfg: Config, R, V, mode: int):
+    """One macro step of Algorithm ClassicETDAlgo: mode 0 with P = 2 pi eps, mode 1
+    (modified ETD) with P = the mean first-tour time.  Returns (R, V, P)."""
+    R, V = _f64(R).copy(), _f64(V).copy()
+    P = np.zeros(1, np.float64)
+    _check(_load().orc_classic_step(C.byref(cfg.to_c()), R.size, _pd(R), _pd(V), int(mode), _pd(P)), "classic_step")
+    return R, V, float(P[0])
 
 
 def quad_root(v0, v1, v2) -> float:

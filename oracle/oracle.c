@@ -638,3 +638,54 @@ double orc_duffing_period_series(double eps, double r0, double v0) {
 double orc_duffing_energy(double eps, double r, double v) {
     return 0.5 * (r * r + v * v) + 0.25 * eps * ((r * r) * (r * r));
 }
+
+/* ------------------------------------------------------------------ */
+/* Classical and modified ETD (Algorithm ClassicETDAlgo)               */
+/* ------------------------------------------------------------------ */
+
+/* Delta t = N P + o with 0 <= o < P; y(t_n + P) by the fine solver from y_n
+   (exactly steps_per_turn fine steps when P = 2 pi eps, otherwise
+   floor(P/h) steps and one step of the rest, as orc_brute_force);
+   y(t_n + N P) = y_n + N (y(t_n + P) - y_n) (eq. step2ClassicalETDAlgo);
+   y(t_{n+1}) by the fine solver over o from y(t_n + N P). */
+int orc_classic_step(const orc_params* p, int64_t n, double* R, double* V, int mode, double* P_out) {
+    orc_derived d;
+    if (orc_derive(p, &d) || n < 0 || (n > 0 && (!R || !V)) || (mode != 0 && mode != 1)) return -1;
+    double P = 2.0 * M_PI * p->eps;
+    int rc = 0;
+    if (mode == 1 && n > 0) {
+        double* T = (double*)malloc((size_t)n * sizeof(double));
+        if (!T) return -2;
+        rc = orc_periods(p, n, R, V, T, NULL, NULL);
+        double sum = 0.0;
+        for (int64_t i = 0; i < n; ++i) sum += T[i];
+        free(T);
+        if (rc) return rc;
+        P = (sum / (double)n) * d.h;
+    }
+    if (P_out) *P_out = P;
+    if (n == 0) return 0;
+    const double o = fmod(p->dt, P);
+    const double N = rint((p->dt - o) / P);
+    double* Rn = (double*)malloc((size_t)n * sizeof(double));
+    double* Vn = (double*)malloc((size_t)n * sizeof(double));
+    if (!Rn || !Vn) {
+        free(Rn);
+        free(Vn);
+        return -2;
+    }
+    memcpy(Rn, R, (size_t)n * sizeof(double));
+    memcpy(Vn, V, (size_t)n * sizeof(double));
+    if (mode == 0) rc = orc_fine_steps(p, n, R, V, d.h, p->steps_per_turn);
+    else rc = orc_brute_force(p, n, R, V, P);
+    if (!rc) {
+        for (int64_t i = 0; i < n; ++i) {
+            R[i] = Rn[i] + N * (R[i] - Rn[i]);
+            V[i] = Vn[i] + N * (V[i] - Vn[i]);
+        }
+        rc = orc_brute_force(p, n, R, V, o);
+    }
+    free(Rn);
+    free(Vn);
+    return rc;
+}

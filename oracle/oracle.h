@@ -85,6 +85,13 @@ int  orc_periods(const orc_params* p, int64_t n, const double* R, const double* 
 int  orc_etd_step(const orc_params* p, int64_t n, double* R, double* V, double* T,
                   int T_known, int64_t* N_out, double* o_out, orc_step_stats* st);
 
+/* One macro step of the classical ETD scheme (Algorithm ClassicETDAlgo) with
+   the period P = 2 pi eps (mode 0) or P = the mean over the particles of the
+   time of their first complete tour (mode 1: the "modified ETD" of Sec. 2,
+   the T_i of Remark CompOfThePeriodsRem averaged in index order).  P_out
+   (may be NULL) receives P (time). */
+int  orc_classic_step(const orc_params* p, int64_t n, double* R, double* V, int mode, double* P_out);
+
 /* Building blocks exposed for the pin tests. */
 double orc_quad_root(double v0, double v1, double v2);
 double orc_interp(double y0, double y1, double y2, double s);

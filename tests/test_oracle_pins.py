@@ -532,3 +532,60 @@ def test_mlp_bf16_rounding_points():
     assert mlp.loss_and_grads(w, X, Y, True)[0] == mlp.loss_and_grads(wb, X, Y, True)[0]
     a = mlp.forward(w, X, True)
     assert np.array_equal(a["h1b"], mlp.bf16(a["h1b"])) and np.array_equal(a["h2b"], mlp.bf16(a["h2b"]))
+
+
+# ------------------------------------------------ classical / modified ETD
+
+
+def test_classic_etd_zero_field_is_the_exact_rotation():
+    # E = 0: the fine solve over 2 pi eps returns to y_n, the extrapolation
+    # keeps it, and the solve over o rotates by o = Delta t mod 2 pi eps:
+    # the exact flow r(Delta t / eps) y_n
+    c = pcfg(field_model=2, dt=0.37)
+    R0, V0 = inputs.gaussian_beam(50, seed=3)
+    for mode in (0, 1):
+        R, V, P = oracle.classic_step(c, R0, V0, mode)
+        th = c.dt / c.eps
+        Rx, Vx = R0 * np.cos(th) + V0 * np.sin(th), -R0 * np.sin(th) + V0 * np.cos(th)
+        assert np.max(np.abs(R - Rx)) < 1e-11 and np.max(np.abs(V - Vx)) < 1e-11
+        assert P == pytest.approx(2 * np.pi * c.eps, rel=1e-12 if mode == 0 else 1e-9)
+
+
+def test_modified_etd_on_one_duffing_orbit():
+    # one particle: the mean first-tour time is its own period, so the step
+    # lands on the fine solution at Delta t within the detection and
+    # interpolation error (the same order as the improved scheme's)
+    c = pcfg(field_model=1, dt=0.5)
+    R0, V0 = np.array([1.3]), np.array([-0.4])
+    R, V, P = oracle.classic_step(c, R0, V0, 1)
+    Rf, Vf = oracle.brute_force(c, R0, V0, c.dt)
+    Tx = oracle.duffing_period_agm(c.eps, 1.3, -0.4)
+    assert P == pytest.approx(Tx, rel=1e-5)
+    assert abs(R[0] - Rf[0]) < 1e-3 and abs(V[0] - Vf[0]) < 1e-3
+
+
+def test_modified_etd_drifts_where_the_improved_scheme_does_not():
+    # Sec. 4.1 (Duffing field, the paper's beam of eq. InitialConditionBeam):
+    # the periods depend on the amplitude, so one mean period mis-times every
+    # particle but the average one and the modified scheme's error grows
+    # faster than linearly, while the improved scheme, with each particle's
+    # own period, grows slowly.  (On a wide beam, r, v ~ N(0, 1), the modified
+    # scheme blows up within a few steps.)
+    c = pcfg(field_model=1, dt=0.5)
+    R0, V0 = inputs.paper_beam(400, seed=8)
+    Rm, Vm = R0, V0
+    Ri, Vi = R0, V0
+    T = oracle.periods(c, R0, V0)[0]
+    errs = {}
+    for k in range(1, 41):
+        Rm, Vm, _ = oracle.classic_step(c, Rm, Vm, 1)
+        res = oracle.etd_step(c, Ri, Vi, T)
+        Ri, Vi = res.R, res.V
+        if k in (10, 40):
+            Rf, Vf = oracle.brute_force(c, R0, V0, k * c.dt)
+            errs[k] = (np.sqrt(np.mean((Rm - Rf) ** 2 + (Vm - Vf) ** 2)),
+                       np.sqrt(np.mean((Ri - Rf) ** 2 + (Vi - Vf) ** 2)))
+    (m10, i10), (m40, i40) = errs[10], errs[40]
+    assert m40 > 8 * m10                 # faster than linear: 4x the time, > 8x the error
+    assert i40 < 5 * i10 and i40 < 1e-3  # about linear
+    assert m40 > 50 * i40
