@@ -137,6 +137,18 @@ int pic_fine_steps(pic_handle* h, int64_t n_fine);
    multiples of h only). */
 int pic_fine_advance(pic_handle* h, double t);
 
+/* Comparator schemes: n_steps macro steps of the classical ETD scheme
+   (Algorithm ClassicETDAlgo): Delta t = N P + o with 0 <= o < P; y(t_n + P)
+   by the fine solver from y_n; y(t_n + N P) = y_n + N (y(t_n + P) - y_n)
+   (eq. step2ClassicalETDAlgo); y(t_{n+1}) by the fine solver over o.
+   period_mode 0: P = 2 pi eps (steps_per_turn fine steps), the classical
+   scheme; 1: P = the mean over the particles of their first-tour time
+   (Remark CompOfThePeriodsRem; at every step, or from pic_init with
+   periods_once), the "modified ETD" scheme of Sec. 2.  Fine solves over a
+   time u: floor(u/h) steps and one step of the rest.  *period (may be NULL)
+   receives the P of the last step (time).  FP64 handles only. */
+int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period);
+
 typedef struct {
     double  t;                 /* time reached                                  */
     int64_t n_steps;           /* macro steps taken                             */

@@ -761,9 +761,8 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
     return PIC_OK;
 }
 
-int pic_fine_advance(pic_handle* h, double t) {
-    if (!h || !(t >= 0.0) || !std::isfinite(t)) return PIC_ERR_INVALID_ARG;
-    if (h->prec) return PIC_ERR_UNSUPPORTED;
+// floor(t/h) fine steps and one step of the rest (FP64 path), time not advanced.
+int fine_advance_raw(pic_handle* h, double t) {
     const long long nfull = (long long)std::floor(t / h->dp.h);
     const double rem = t - (double)nfull * h->dp.h;
     int rc = PIC_OK;
@@ -774,7 +773,77 @@ int pic_fine_advance(pic_handle* h, double t) {
         rc = run_window(h, pic::MODE_FINE, 1);
         h->dp = saved;
     }
+    return rc;
+}
+
+int pic_fine_advance(pic_handle* h, double t) {
+    if (!h || !(t >= 0.0) || !std::isfinite(t)) return PIC_ERR_INVALID_ARG;
+    if (h->prec) return PIC_ERR_UNSUPPORTED;
+    const int rc = fine_advance_raw(h, t);
     if (!rc) h->t += t;
+    return rc;
+}
+
+int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period) {
+    if (!h || n_steps < 0 || (period_mode != 0 && period_mode != 1)) return PIC_ERR_INVALID_ARG;
+    if (h->prec) return PIC_ERR_UNSUPPORTED;
+    const size_t bytes = (size_t)h->n * sizeof(double2);
+    int rc = PIC_OK;
+    if (h->n > 0 && !h->y_prev) {
+        char* yp = nullptr;
+        rc = dalloc(h, &yp, bytes);
+        if (rc) return rc;
+        h->y_prev = yp;
+    }
+    std::vector<double> Th;
+    for (long long s = 0; s < n_steps && !rc; ++s) {
+        double P = 2.0 * kPi * h->prm.eps;
+        if (period_mode == 1 && h->n > 0) {
+            // mean over the particles of their first-tour time (Remark
+            // CompOfThePeriodsRem), summed in the public order
+            const double* Tsrc = h->B.T;
+            if (h->prm.periods_once) {
+                Tsrc = h->Tin;
+            } else {
+                rc = run_window(h, pic::MODE_PERIODS, 0);
+                if (rc) break;
+            }
+            Th.resize((size_t)h->n);
+            cudaError_t e = pic::launch_permute_d(Tsrc, h->perm, h->n, 1.0, 1, h->tmpR, h->sm_count, h->st, &h->launches);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(Th.data(), h->tmpR, sizeof(double) * Th.size(), cudaMemcpyDeviceToHost, h->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            if (e != cudaSuccess) {
+                rc = map_cuda(e);
+                break;
+            }
+            double sum = 0.0;
+            for (double x : Th) sum += x;
+            P = (sum / (double)h->n) * h->dp.h;
+        }
+        if (period) *period = P;
+        const double o = std::fmod(h->prm.dt, P);
+        const double N = std::rint((h->prm.dt - o) / P);
+        if (h->n > 0) {
+            cudaError_t e = cudaMemcpyAsync(h->y_prev, h->B.y, bytes, cudaMemcpyDeviceToDevice, h->st);
+            if (e != cudaSuccess) {
+                rc = map_cuda(e);
+                break;
+            }
+            // y(t_n + P), then y(t_n + N P) = y_n + N (y(t_n + P) - y_n), then the rest o
+            rc = period_mode == 0 ? run_window(h, pic::MODE_FINE, h->prm.steps_per_turn) : fine_advance_raw(h, P);
+            if (rc) break;
+            e = pic::launch_extrapolate_classic(h->B.y, (const double2*)h->y_prev, h->n, N, h->sm_count, h->st,
+                                                &h->launches);
+            if (e != cudaSuccess) {
+                rc = map_cuda(e);
+                break;
+            }
+            rc = fine_advance_raw(h, o);
+            if (rc) break;
+        }
+        h->t += h->prm.dt;
+        h->n_steps += 1;
+    }
     return rc;
 }
 

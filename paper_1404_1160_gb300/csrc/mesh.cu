@@ -252,12 +252,28 @@ __global__ void k_unpack(const double2* __restrict__ y, double* __restrict__ R, 
     }
 }
 
+// y = y0 + N (y - y0) (eq. step2ClassicalETDAlgo), element by element.
+__global__ void k_extrapolate_classic(double2* __restrict__ y, const double2* __restrict__ y0, long long n, double N) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 a = y0[i], b = y[i];
+        y[i] = make_double2(a.x + N * (b.x - a.x), a.y + N * (b.y - a.y));
+    }
+}
+
 // ------------------------------------------------------------ host launchers
 
 static int grid_for(long long n, int sm_count) {
     long long want = (n + 255) / 256;
     long long cap = (long long)sm_count * 8;
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+cudaError_t launch_extrapolate_classic(double2* y, const double2* y0, long long n, double N, int sm_count,
+                                       cudaStream_t st, long long* launches) {
+    if (n == 0) return cudaSuccess;
+    k_extrapolate_classic<<<grid_for(n, sm_count), 256, 0, st>>>(y, y0, n, N);
+    if (launches) ++*launches;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const double* R, const double* V, double2* y, long long n, int sm_count, cudaStream_t st,

@@ -32,6 +32,8 @@ cudaError_t launch_deposit(const DevParams& P, const double* R, long long n, int
                            long long* n_out, cudaStream_t st, int sm_count, long long* launches);
 cudaError_t launch_pack(const double* R, const double* V, double2* y, long long n, int sm_count, cudaStream_t st,
                         long long* launches);
+cudaError_t launch_extrapolate_classic(double2* y, const double2* y0, long long n, double N, int sm_count,
+                                       cudaStream_t st, long long* launches);
 cudaError_t launch_unpack(const double2* y, double* R, double* V, long long n, int sm_count, cudaStream_t st,
                           long long* launches);
 cudaError_t launch_poisson(const DevParams& P, const long long* Q, double* E, double* edges,

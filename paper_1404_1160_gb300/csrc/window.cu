@@ -493,6 +493,11 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     }
 
     if (blockIdx.x == 0 && threadIdx.x == 0 && !fine_only) *B.K_out = K;
+    if (detect_only) {
+        // step 1 alone leaves y^n as it was: it is row 0 of the trajectory
+        for (long long i = i0; i < n; i += stride) B.y[i] = B.traj[i];
+        return;
+    }
     if (mode != MODE_ETD) return;
 
     // ---- landing (step 3) and extrapolation (step 4)

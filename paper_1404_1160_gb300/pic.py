@@ -156,6 +156,7 @@ def load() -> C.CDLL:
             "pic_mlp_destroy": (None, [vp]),
             "pic_step_learned": (i32, [H, vp, i64, C.c_float, C.c_float, d, P(i64)]),
             "pic_fine_advance": (i32, [H, d]),
+            "pic_step_classic": (i32, [H, i64, i32, P(d)]),
             "pic_batch_create": (i32, [i32, P(pic_params), P(i64), P(C.c_void_p), P(C.c_void_p), vp, P(vp)]),
             "pic_batch_step": (i32, [vp, i64]),
             "pic_batch_set_config": (i32, [vp, i32, i32, d, i32]),
@@ -541,3 +542,10 @@ def pic_batch_steps(b: Batch) -> int:
 
 def pic_batch_launch_count(b: Batch) -> int:
     return int(load().pic_batch_launch_count(b.ptr))
+
+
+def pic_step_classic(h: Handle, n_steps: int, period_mode: int) -> float:
+    """Classical (mode 0) or modified (mode 1) ETD macro steps; returns the last period used (time)."""
+    P = C.c_double(0.0)
+    _check(load().pic_step_classic(h.ptr, int(n_steps), int(period_mode), C.byref(P)), "pic_step_classic")
+    return float(P.value)

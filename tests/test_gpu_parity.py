@@ -191,6 +191,31 @@ def test_duffing_config0_shape_matches_oracle(solver):
     pic.pic_destroy(h)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_poisson_periods_once_keeps_the_initial_state(prec):
+    # step 1 alone at initialisation (periods_once) must leave y^0 untouched,
+    # and the steps that follow use the periods of y^0
+    p = pic.pic_default_params(periods_once=1, precision=prec)
+    R0, V0 = inputs.gaussian_beam(5000, seed=13, r_cut=4.0)
+    if prec:
+        R0, V0 = R0.astype(np.float32).astype(np.float64), V0.astype(np.float32).astype(np.float64)
+    h = pic.pic_init(p, R0, V0)
+    R, V = pic.pic_get_particles(h)
+    assert bit_equal(R, R0) and bit_equal(V, V0)
+    st = pic.pic_get_state(h)
+    T, _, _ = oracle.periods(cfg_of(p), R0, V0)
+    if prec == 0:
+        assert bit_equal(st["T"], T)
+        pic.pic_step(h, 2)
+        R, V = pic.pic_get_particles(h)
+        res = oracle.etd_step(cfg_of(p), R0, V0, T)
+        res = oracle.etd_step(cfg_of(p), res.R, res.V, T)
+        assert bit_equal(R, res.R) and bit_equal(V, res.V)
+    else:
+        assert np.max(np.abs(st["T"] - T)) < 2e-4
+    pic.pic_destroy(h)
+
+
 @pytest.mark.parametrize("field", [pic.PIC_FIELD_DUFFING, pic.PIC_FIELD_ZERO])
 def test_local_field_periods_every_step(field):
     # periods recomputed every macro step, dt = 0.5 (N about 8), with one
