@@ -48,6 +48,13 @@ WORKLOADS = {
     # Duffing test field, periods once at init
     "duffing1e4": dict(n=10**4, params=dict(field_model=1, dt=0.05, periods_once=1), r_cut=None,
                        desc="Duffing E=-r^3, eps=0.01, N_p=1e4, dt=0.05, periods once, FP64"),
+    # comparator schemes (Algorithm ClassicETDAlgo) on the same beam as vp1e6
+    "vp1e6_classical": dict(n=10**6, params=dict(), r_cut=4.0, scheme=0,
+                            desc="Classical ETD (P = 2 pi eps), Vlasov-Poisson, eps=0.01, N_p=1e6, N_r=256 on [-4,4], "
+                                 "dt=0.1, Lawson RK4 fine solver, FP64"),
+    "vp1e6_modified": dict(n=10**6, params=dict(), r_cut=4.0, scheme=1,
+                           desc="Modified ETD (P = mean first-tour time), Vlasov-Poisson, eps=0.01, N_p=1e6, N_r=256 "
+                                "on [-4,4], dt=0.1, Lawson RK4 fine solver, FP64"),
     # learned stepper: network-corrected improved-ETD steps of dt = 0.4 (FP32 form underneath)
     "learned1e7": dict(n=10**7, params=dict(precision=1, dt=0.4, n_cells=512, sort_every=4), r_cut=4.0,
                        learned=dict(train_n=100_000, train_macro=3, steps=1500, batch=8192, tol=1e-4, eval_n=20_000),
@@ -215,8 +222,12 @@ def run_ours(args):
     h = pic.pic_init(prm, torch.from_numpy(R0).cuda(), torch.from_numpy(V0).cuda(), stream)
     n_fb = [0]
 
+    scheme = wl.get("scheme")
+
     def do_step():
-        if net is None:
+        if scheme is not None:
+            pic.pic_step_classic(h, 1, scheme)
+        elif net is None:
             pic.pic_step(h, 1)
         else:
             n_fb[0] += pic.pic_step_learned(h, net, 1, scale=tuple(out_scale), drift_tol=lw["tol"])
@@ -288,7 +299,7 @@ def run_ours(args):
                     "kernel": "k_window32_coop (FP32 form, one launch per macro step)",
                     "kernel_ms": kern_ms, "fine_steps_per_launch": K, "algorithmic_bytes_per_launch": bytes_,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
-    elif prm.field_model == 0 and kernel_ms:
+    elif prm.field_model == 0 and kernel_ms and scheme is None:
         kern_ms = float(np.mean(kernel_ms))
         flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
         achieved = flops / (kern_ms / 1e3)
@@ -563,8 +574,11 @@ def cpu_baseline(workload: str, n_sample: int):
     steps = 0
     R, V = R0, V0
     while True:
-        res = oracle.etd_step(cfg, R, V, T)
-        R, V = res.R, res.V
+        if "scheme" in wl:
+            R, V, _ = oracle.classic_step(cfg, R, V, wl["scheme"])
+        else:
+            res = oracle.etd_step(cfg, R, V, T)
+            R, V = res.R, res.V
         steps += 1
         el = time.perf_counter() - t0
         if el > 8.0 or steps >= 1000:
@@ -619,13 +633,17 @@ def run_reference(args):
     cfg = oracle_cfg(args.workload)
     R, V = inputs.gaussian_beam(n, seed=0, r_cut=wl["r_cut"])
     T = oracle.periods(cfg, R, V)[0] if cfg_periods_once(args.workload) else None
-    for _ in range(args.warmup):
+    def one(R, V):
+        if "scheme" in wl:
+            return oracle.classic_step(cfg, R, V, wl["scheme"])[:2]
         res = oracle.etd_step(cfg, R, V, T)
-        R, V = res.R, res.V
+        return res.R, res.V
+
+    for _ in range(args.warmup):
+        R, V = one(R, V)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        res = oracle.etd_step(cfg, R, V, T)
-        R, V = res.R, res.V
+        R, V = one(R, V)
     el = time.perf_counter() - t0
     value = n * args.steps / el
     line = {
