@@ -146,8 +146,11 @@ int pic_fine_advance(pic_handle* h, double t);
    (Remark CompOfThePeriodsRem; at every step, or from pic_init with
    periods_once), the "modified ETD" scheme of Sec. 2.  Fine solves over a
    time u: floor(u/h) steps and one step of the rest.  *period (may be NULL)
-   receives the P of the last step (time).  FP64 handles only. */
-int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period);
+   receives the P of the last step (time); *fine_steps (may be NULL) the
+   fine steps its windows ran over all n_steps (the partial steps and the
+   period-detection windows included).  pic_window_time then reports all
+   its window launches.  FP64 handles only. */
+int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period, int64_t* fine_steps);
 
 typedef struct {
     double  t;                 /* time reached                                  */
@@ -202,7 +205,8 @@ int pic_get_state(pic_handle* h, pic_state_t* out);
 int pic_set_state(pic_handle* h, const pic_state_t* in);
 
 /* Device time (CUDA events on the handle's stream) of the window kernel
-   launches of the last pic_step call, and their number.  Host only. */
+   launches of the last pic_step (or pic_step_classic) call, and their
+   number.  Host only. */
 int pic_window_time(const pic_handle* h, double* ms, int64_t* launches);
 
 int64_t pic_num_particles(const pic_handle* h);

@@ -234,6 +234,12 @@ struct pic_handle {
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
     double window_ms = 0.0;
+    int64_t window_n = 0;
+    // sums over the windows of one pic_step_classic call
+    bool acc_on = false;
+    double acc_ms = 0.0;
+    int64_t acc_n = 0;
+    int64_t acc_fine = 0;
 };
 
 namespace {
@@ -296,6 +302,11 @@ void collect_window_ms(pic_handle* h) {
         if (cudaEventElapsedTime(&x, h->ev[k], h->ev[k + 1]) == cudaSuccess) ms += x;
     }
     h->window_ms = ms;
+    h->window_n = h->ev_used / 2;
+    if (h->acc_on) {
+        h->acc_ms += ms;
+        h->acc_n += h->window_n;
+    }
 }
 
 // Phase-space sort of the storage order before a window (see sort.cu).
@@ -346,6 +357,7 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     if (e != cudaSuccess) return map_cuda(e);
     const int rc = read_status(h);
     collect_window_ms(h);
+    if (h->acc_on && mode == pic::MODE_FINE) h->acc_fine += n_iter;
     return rc;
 }
 
@@ -784,7 +796,7 @@ int pic_fine_advance(pic_handle* h, double t) {
     return rc;
 }
 
-int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period) {
+int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double* period, int64_t* fine_steps) {
     if (!h || n_steps < 0 || (period_mode != 0 && period_mode != 1)) return PIC_ERR_INVALID_ARG;
     if (h->prec) return PIC_ERR_UNSUPPORTED;
     const size_t bytes = (size_t)h->n * sizeof(double2);
@@ -796,6 +808,10 @@ int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double
         h->y_prev = yp;
     }
     std::vector<double> Th;
+    h->acc_on = true;
+    h->acc_ms = 0.0;
+    h->acc_n = 0;
+    h->acc_fine = 0;
     for (long long s = 0; s < n_steps && !rc; ++s) {
         double P = 2.0 * kPi * h->prm.eps;
         if (period_mode == 1 && h->n > 0) {
@@ -809,9 +825,13 @@ int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double
                 if (rc) break;
             }
             Th.resize((size_t)h->n);
+            long long K_det = 0;  // fine steps of the detection window
             cudaError_t e = pic::launch_permute_d(Tsrc, h->perm, h->n, 1.0, 1, h->tmpR, h->sm_count, h->st, &h->launches);
             if (e == cudaSuccess) e = cudaMemcpyAsync(Th.data(), h->tmpR, sizeof(double) * Th.size(), cudaMemcpyDeviceToHost, h->st);
+            if (e == cudaSuccess && !h->prm.periods_once)
+                e = cudaMemcpyAsync(&K_det, h->B.K_out, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+            h->acc_fine += K_det;
             if (e != cudaSuccess) {
                 rc = map_cuda(e);
                 break;
@@ -844,6 +864,10 @@ int pic_step_classic(pic_handle* h, int64_t n_steps, int32_t period_mode, double
         h->t += h->prm.dt;
         h->n_steps += 1;
     }
+    h->acc_on = false;
+    h->window_ms = h->acc_ms;
+    h->window_n = h->acc_n;
+    if (fine_steps) *fine_steps = h->acc_fine;
     return rc;
 }
 
@@ -923,7 +947,7 @@ int pic_moments(pic_handle* h, pic_moments_t* out) {
         out->window_steps = Kw;
     }
     out->window_ms = h->window_ms;
-    out->window_launches = h->ev_used / 2;
+    out->window_launches = h->window_n;
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         std::vector<int64_t> Q((size_t)h->dp.n_cells + 1);
         int64_t nout = 0;
@@ -1059,7 +1083,7 @@ int pic_set_state(pic_handle* h, const pic_state_t* in) {
 int pic_window_time(const pic_handle* h, double* ms, int64_t* launches) {
     if (!h) return PIC_ERR_INVALID_ARG;
     if (ms) *ms = h->window_ms;
-    if (launches) *launches = h->ev_used / 2;
+    if (launches) *launches = h->window_n;
     return PIC_OK;
 }
 

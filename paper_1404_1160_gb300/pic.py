@@ -156,7 +156,7 @@ def load() -> C.CDLL:
             "pic_mlp_destroy": (None, [vp]),
             "pic_step_learned": (i32, [H, vp, i64, C.c_float, C.c_float, d, P(i64)]),
             "pic_fine_advance": (i32, [H, d]),
-            "pic_step_classic": (i32, [H, i64, i32, P(d)]),
+            "pic_step_classic": (i32, [H, i64, i32, P(d), P(i64)]),
             "pic_batch_create": (i32, [i32, P(pic_params), P(i64), P(C.c_void_p), P(C.c_void_p), vp, P(vp)]),
             "pic_batch_step": (i32, [vp, i64]),
             "pic_batch_set_config": (i32, [vp, i32, i32, d, i32]),
@@ -324,7 +324,7 @@ def pic_set_state(h: Handle, state: dict) -> None:
 
 
 def pic_window_time(h: Handle):
-    """(device ms, launches) of the window kernels of the last pic_step call."""
+    """(device ms, launches) of the window kernels of the last pic_step (or pic_step_classic) call."""
     ms = C.c_double()
     k = C.c_int64()
     _check(load().pic_window_time(h.ptr, C.byref(ms), C.byref(k)), "pic_window_time")
@@ -544,8 +544,11 @@ def pic_batch_launch_count(b: Batch) -> int:
     return int(load().pic_batch_launch_count(b.ptr))
 
 
-def pic_step_classic(h: Handle, n_steps: int, period_mode: int) -> float:
-    """Classical (mode 0) or modified (mode 1) ETD macro steps; returns the last period used (time)."""
+def pic_step_classic(h: Handle, n_steps: int, period_mode: int, with_fine_steps: bool = False):
+    """Classical (mode 0) or modified (mode 1) ETD macro steps; returns the
+    last period used (time), and with `with_fine_steps` also the fine steps
+    the call's windows ran."""
     P = C.c_double(0.0)
-    _check(load().pic_step_classic(h.ptr, int(n_steps), int(period_mode), C.byref(P)), "pic_step_classic")
-    return float(P.value)
+    K = C.c_int64(0)
+    _check(load().pic_step_classic(h.ptr, int(n_steps), int(period_mode), C.byref(P), C.byref(K)), "pic_step_classic")
+    return (float(P.value), int(K.value)) if with_fine_steps else float(P.value)
