@@ -79,9 +79,30 @@ __device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, i
 // Field tables of one cycle (two fields) from the cycle's global charge:
 // trapezoid integral from r = 0 (S_j = g_j - g_c), E_j = S_j q_unit/2 * (1/r_j),
 // E_c = Q_c q_unit / h_r, then (E_j, (E_{j+1}-E_j)/W) per cell.
+// stop_src (may be null): the not-done count of the cycle, read together with
+// the charge; *s_stop = (count == 0) after the call.
 __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, long long* q, long long* g,
-                             double2* tab, const double* inv_r, double* edges, long long* s_warp) {
+                             double2* tab, const double* inv_r, double* edges, long long* s_warp,
+                             const int* stop_src = nullptr, int* s_stop = nullptr) {
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
+    if (stop_src && threadIdx.x == 0) *s_stop = (__ldcg(stop_src) == 0);
+    auto emit = [&](int f, int j, double e, double en, long long S) {
+        double sl = 0.0;
+        if (j < Nc) {
+            const double d = en - e;
+            // d / W: exponent shift when the result stays normal (exact), else multiply
+            const int ex = (int)((__double_as_longlong(d) >> 52) & 0x7ff);
+            sl = (ex > P.log2W + 1 && ex < 0x7ff) ? scale_pow2(d, -P.log2W) : d * P.invW;
+        }
+        tab[f * Np1 + j] = make_double2(e, sl);
+        if (j == 0) edges[2 * f] = i64_to_double(S) * P.q_half;
+        if (j == Nc) edges[2 * f + 1] = i64_to_double(S) * P.q_half;
+    };
+    if (field_build_regs(P, Qg, inv_r, s_warp, emit)) {
+        __syncthreads();
+        return;
+    }
+    // staged build (meshes too large for the register form)
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + (size_t)idx * kQPad);
     __syncthreads();
     block_exscan_pairs2(q, g, Nc, s_warp);
@@ -410,15 +431,12 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
         if (blockIdx.x == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
         if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok, gridDim.x)) return;
-        if (!fine_only) {
-            if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
-            __syncthreads();
-            if (s_stop) {
-                K = k;
-                break;
-            }
+        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tab, inv_r, s_edges, s_warp,
+                     fine_only ? nullptr : &B.notdone[k % 3], &s_stop);
+        if (!fine_only && s_stop) {
+            K = k;
+            break;
         }
-        build_fields(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tab, inv_r, s_edges, s_warp);
         ++cyc;
 
         // ---- sweep B(k): gather pair 1, deposit stage pair 2

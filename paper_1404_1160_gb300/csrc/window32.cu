@@ -90,9 +90,23 @@ __device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, 
 // E_c = Q_c q_unit / h_r, rounded once to binary32 together with the
 // differences E_{j+1} - E_j.  q is the int64 scan input (2 Np1), g the scan
 // output, reused for E in FP64.
+// stop_src (may be null): the not-done count of the cycle, read together with
+// the charge; *s_stop = (count == 0) after the call.
 __device__ void build_fields32(const DevParams& P, const unsigned long long* Qg, long long* q, long long* g,
-                               float2* tab, const double* inv_r, float* edges, long long* s_warp, long long* s_c) {
+                               float2* tab, const double* inv_r, float* edges, long long* s_warp, long long* s_c,
+                               const int* stop_src = nullptr, int* s_stop = nullptr) {
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
+    if (stop_src && threadIdx.x == 0) *s_stop = (__ldcg(stop_src) == 0);
+    auto emit = [&](int f, int j, double e, double en, long long S) {
+        tab[f * Np1 + j] = make_float2((float)e, j < Nc ? (float)(en - e) : 0.0f);
+        if (j == 0) edges[2 * f] = (float)(i64_to_double(S) * P.q_half);
+        if (j == Nc) edges[2 * f + 1] = (float)(i64_to_double(S) * P.q_half);
+    };
+    if (field_build_regs(P, Qg, inv_r, s_warp, emit)) {
+        __syncthreads();
+        return;
+    }
+    // staged build (meshes too large for the register form)
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) q[idx] = (long long)__ldcg(Qg + (size_t)idx * kQPad);
     __syncthreads();
     block_exscan_pairs2(q, g, Nc, s_warp);
@@ -407,16 +421,12 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
         if (lb == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
         if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok, (unsigned int)nb)) return;
-        if (track) {
-            if (threadIdx.x == 0) s_stop = (__ldcg(&B.notdone[k % 3]) == 0);
-            __syncthreads();
-            if (s_stop) {
-                K = k;
-                break;
-            }
-        }
         build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabA, inv_r, s_edA,
-                       s_warp, s_c);
+                       s_warp, s_c, track ? &B.notdone[k % 3] : nullptr, &s_stop);
+        if (track && s_stop) {
+            K = k;
+            break;
+        }
         ++cyc;
 
         // ---- sweep B(k): gather pair 1 of step k, deposit stage pair 2

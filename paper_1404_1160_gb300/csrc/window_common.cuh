@@ -61,47 +61,142 @@ static __device__ void block_exscan_pairs2(const long long* q, long long* g, int
     __syncthreads();
 }
 
+// Charge to field of one cycle for both fields, with the nodes in registers
+// (three block barriers and no shared staging).  The first half of the
+// block takes field 0, the second field 1; in warp w of a half, lane l < 31
+// owns the R nodes j = (31 w + l) R + r, r < R, and lane 31 repeats the
+// first nodes of the next warp, so that every lane finds E_{j+1} of its
+// last node in the next lane.  q_j comes from the cycle's global charge Qg;
+// the exact trapezoid sums g_j = sum_{m<j} (q_m + q_{m+1}) are a warp scan
+// plus the totals of the preceding warps (s_tot), S_j = g_j - g_c, and
+//   E_j = (S_j q_unit/2) (1/r_j),  E_c = (q_c q_unit) (1/h_r),
+// the same operations in the same order as the staged build.  Each owned
+// node is passed to emit(f, j, E_j, E_{j+1}, S_j) (E_{j+1} unused at
+// j = n_cells).  Covers n_cells + 1 <= 31 R (blockDim/64) nodes; returns
+// false (doing nothing) when R = 4 would not suffice.  s_tot: 64 int64.
+template <int R, class Emit>
+static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, const unsigned long long* Qg,
+                                                          const double* inv_r, long long* s_tot, Emit emit) {
+    const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
+    const int H = blockDim.x >> 1;
+    const int f = threadIdx.x >= H ? 1 : 0;
+    const int u = threadIdx.x - f * H, lane = threadIdx.x & 31, w = u >> 5;
+    const int j0 = (w * 31 + lane) * R;
+    const unsigned long long* Qf = Qg + (size_t)f * Np1 * kQPad;
+    long long q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) q[r] = (j0 + r <= Nc) ? (long long)__ldcg(Qf + (size_t)(j0 + r) * kQPad) : 0ll;
+    const long long qn = __shfl_down_sync(0xffffffffu, q[0], 1);
+    long long L = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long right = (r + 1 < R) ? q[(r + 1) % R] : qn;
+        L += (j0 + r < Nc) ? q[r] + right : 0ll;
+    }
+    if (lane == 31) L = 0;  // its nodes belong to the next warp
+    const long long incl = warp_incl_scan64(L);
+    if (lane == 31) s_tot[f * 32 + w] = incl;
+    __syncthreads();
+    long long g0 = incl - L;
+    for (int v = 0; v < w; ++v) g0 += s_tot[f * 32 + v];
+    {
+        long long g = g0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (lane != 31 && j0 + r == c) s_tot[f * 32 + 16] = g;
+            if (r + 1 < R) g += (j0 + r < Nc) ? q[r] + q[(r + 1) % R] : 0ll;
+        }
+    }
+    __syncthreads();
+    const long long gc = s_tot[f * 32 + 16];
+    auto field_at = [&](int j, long long S, long long qj) -> double {
+        if (j > Nc) return 0.0;
+        if (j == c) return (i64_to_double(qj) * P.q_unit) * P.inv_hr;
+        return (i64_to_double(S) * P.q_half) * inv_r[j];
+    };
+    long long S = g0 - gc;
+    double Ecur = field_at(j0, S, q[0]);
+    const double En = __shfl_down_sync(0xffffffffu, Ecur, 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = j0 + r;
+        long long Sn = S;
+        double Enext = En;
+        if (r + 1 < R) {
+            Sn = S + ((j < Nc) ? q[r] + q[(r + 1) % R] : 0ll);
+            Enext = field_at(j + 1, Sn, q[(r + 1) % R]);
+        }
+        if (lane != 31 && j <= Nc) emit(f, j, Ecur, Enext, S);
+        Ecur = Enext;
+        S = Sn;
+    }
+}
+
+template <class Emit>
+static __device__ __forceinline__ bool field_build_regs(const DevParams& P, const unsigned long long* Qg,
+                                                        const double* inv_r, long long* s_tot, Emit emit) {
+    const int per_pass = 31 * (int)(blockDim.x >> 6);  // nodes covered per node of a thread
+    const int Np1 = P.n_cells + 1;
+    if ((blockDim.x & 63) != 0 || blockDim.x > 1024) return false;
+    if (Np1 <= per_pass) field_build_regs_r<1>(P, Qg, inv_r, s_tot, emit);
+    else if (Np1 <= 2 * per_pass) field_build_regs_r<2>(P, Qg, inv_r, s_tot, emit);
+    else if (Np1 <= 3 * per_pass) field_build_regs_r<3>(P, Qg, inv_r, s_tot, emit);
+    else if (Np1 <= 4 * per_pass) field_build_regs_r<4>(P, Qg, inv_r, s_tot, emit);
+    else return false;
+    return true;
+}
+
 // Barrier of the n_blocks blocks that share `bar` (the whole grid, or the
-// blocks of one beam of a batch), with a time limit; false if any block
-// timed out or failed.
-// Arrivals count on bar[0]; the last block of a generation publishes the
-// generation number in bar[32] (another cache line), which the others poll.
-static __device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& gen,
-                                          int* status, int* s_ok, unsigned int n_blocks) {
+// blocks of one beam of a batch), with a time limit, in two halves so that
+// a block can issue work that does not depend on the other blocks (loads of
+// its own particles) between its arrival and its wait.
+// Arrival: after the block's own barrier, one release reduction on the
+// counter bar[0] (it orders every write the block made before it, the
+// charge flush included, without waiting for a returned value).  Wait: one
+// thread polls the counter with acquire loads until all n_blocks arrivals of
+// this generation are in; the block barrier then passes the acquire on to
+// the other threads.  The counter only grows within a launch (reset between
+// launches), so generation g waits for g * n_blocks arrivals.
+static __device__ __forceinline__ void grid_arrive(unsigned int* bar, unsigned int& gen) {
     __syncthreads();
     ++gen;
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+}
+
+// false if any block timed out or failed
+static __device__ __forceinline__ bool grid_wait(const DevParams& P, unsigned int* bar, unsigned int gen, int* status,
+                                                 int* s_ok, unsigned int n_blocks) {
     if (threadIdx.x == 0) {
         const unsigned int target = gen * (n_blocks + P.bar_extra);
-        __threadfence();
-        const unsigned int old = atomicAdd(bar, 1u);
         int ok = 1;
-        if (old + 1 == target) {
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 32), "r"(gen) : "memory");
-        } else {
-            long long t0 = 0;
-            unsigned spins = 0;
-            while ((int)(ld_acquire_u32(bar + 32) - gen) < 0) {
-                if ((++spins & 31) == 0) {
-                    if (ld_acquire_s32(status) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    const long long now = global_ns();
-                    if (t0 == 0) {
-                        t0 = now;
-                    } else if (now - t0 > P.wait_ns) {
-                        atomicCAS(status, 0, (int)DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        long long t0 = 0;
+        unsigned spins = 0;
+        while ((int)(ld_acquire_u32(bar) - target) < 0) {
+            if ((++spins & 31) == 0) {
+                if (ld_acquire_s32(status) != 0) {
+                    ok = 0;
+                    break;
+                }
+                const long long now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > P.wait_ns) {
+                    atomicCAS(status, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+static __device__ __forceinline__ bool grid_sync(const DevParams& P, unsigned int* bar, unsigned int& gen,
+                                                 int* status, int* s_ok, unsigned int n_blocks) {
+    grid_arrive(bar, gen);
+    return grid_wait(P, bar, gen, status, s_ok, n_blocks);
 }
 
 // ---- asynchronous copies global -> shared (cp.async, sm_80+)
