@@ -1248,6 +1248,7 @@ cudaError_t batch_upload(pic_batch* b) {
         pic_handle* h = b->hs[i];
         pic::BeamDesc32& d = b->desc[i];
         d.P = h->dp;
+        d.P.hist_copies = 1;  // the batch's shared memory holds one histogram per field
         d.B = h->B32;
         d.Tin = h->prm.periods_once ? h->Tin32 : nullptr;
         d.T_known = h->prm.periods_once ? 1 : 0;

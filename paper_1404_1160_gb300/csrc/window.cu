@@ -54,9 +54,9 @@ __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cel
 }
 
 // Node charge of one field from the block histogram, summed over its
-// `copies` copies `stride` words apart (warp w deposits into copy
-// w % copies, so a hot cell at the beam centre is updated on several
-// addresses instead of one).
+// `copies` copies `stride` words apart (lane l deposits into copy
+// l % copies, so a cell shared by the lanes of a warp is updated on
+// several addresses instead of one).
 template <int HIST>
 __device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, int Np1, int j, long long W, int stride,
                                                         int copies) {
@@ -289,7 +289,9 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     // counter, so they finish a sweep together.
     const int lane = threadIdx.x & 31;
     const long long n_chunks = (n + 31) / 32;
-    unsigned int* const my_hist = hist + ((threadIdx.x >> 5) % copies) * 2 * words;
+    // lane l deposits into copy l mod copies (the lanes of a warp hold
+    // phase-space neighbours, which mostly share a cell)
+    unsigned int* const my_hist = hist + ((threadIdx.x & 31) % copies) * 2 * words;
     Stage* const my_stage = stage + 2 * (threadIdx.x >> 5);
     const long long n_warps = (long long)gridDim.x * (blockDim.x >> 5);
     const long long g_warp = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;

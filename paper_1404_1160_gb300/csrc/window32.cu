@@ -32,6 +32,7 @@ constexpr int kW32Threads = 1024;
 constexpr int kG = 4;             // consecutive particles per lane in a group
 constexpr int kGroup = 32 * kG;   // particles per warp group
 constexpr int kHist32Words = 4;   // 32-bit words per node and field
+constexpr int kHist32CopiesMax = 4;  // histogram copies (lane l deposits into copy l mod copies)
 
 // ---------------------------------------------------------------- deposit
 
@@ -58,13 +59,19 @@ __device__ __forceinline__ unsigned long long hist32_S(const unsigned int* h, in
            ((unsigned long long)h[3 * Np1 + j] << 22);
 }
 
-__device__ __forceinline__ unsigned long long hist32_node(const unsigned int* h, int Np1, int j, long long W) {
+// Node charge from the `copies` copies of a field's histogram, `stride`
+// words apart.
+__device__ __forceinline__ unsigned long long hist32_node(const unsigned int* h, int Np1, int j, long long W,
+                                                          int copies, int stride) {
     unsigned long long C = 0, Sj = 0, Sm = 0;
-    if (j < Np1 - 1) {
-        C = h[j];
-        Sj = hist32_S(h, Np1, j);
+    for (int cp = 0; cp < copies; ++cp) {
+        const unsigned int* hc = h + cp * stride;
+        if (j < Np1 - 1) {
+            C += hc[j];
+            Sj += hist32_S(hc, Np1, j);
+        }
+        if (j >= 1) Sm += hist32_S(hc, Np1, j - 1);
     }
-    if (j >= 1) Sm = hist32_S(h, Np1, j - 1);
     return C * (unsigned long long)W - Sj + Sm;
 }
 
@@ -76,7 +83,8 @@ __device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, 
     unsigned long long* Qg = B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad;
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
-        const unsigned long long v = hist32_node(hist + f * kHist32Words * Np1, Np1, j, P.W);
+        const unsigned long long v =
+            hist32_node(hist + f * kHist32Words * Np1, Np1, j, P.W, P.hist_copies, 2 * kHist32Words * Np1);
         if (v) atomicAdd(Qg + (size_t)idx * kQPad, v);
     }
     if (lb == 0) {
@@ -264,9 +272,9 @@ __device__ __forceinline__ unsigned int grp_tr(const Grp32& G, int q) {
 }
 
 // Shared memory of the FP32 window kernel (bytes).
-static size_t coop32_smem_bytes(int n_cells) {
+static size_t coop32_smem_bytes(int n_cells, int copies) {
     const size_t Np1 = (size_t)n_cells + 1;
-    return 2 * kHist32Words * Np1 * sizeof(unsigned int)  // histograms; also the int64 scan input
+    return (size_t)copies * 2 * kHist32Words * Np1 * sizeof(unsigned int)  // histograms; also the int64 scan input
            + 2 * Np1 * sizeof(long long)                  // scan output, then E in FP64
            + Np1 * sizeof(double)                         // 1/r_j
            + 4 * Np1 * sizeof(float2);                    // tables of pair 1 and pair 2
@@ -279,8 +287,9 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
                                                    unsigned char* smem_raw) {
     const int Nc = P.n_cells, Np1 = Nc + 1;
     const int hw = kHist32Words * Np1;
-    unsigned int* hist = (unsigned int*)smem_raw;  // 2 fields x hw words
-    long long* g = (long long*)(hist + 2 * hw);     // 2 Np1
+    const int copies = P.hist_copies;
+    unsigned int* hist = (unsigned int*)smem_raw;  // copies x 2 fields x hw words
+    long long* g = (long long*)(hist + copies * 2 * hw);  // 2 Np1
     double* inv_r = (double*)(g + 2 * Np1);         // Np1
     float2* tabA = (float2*)(inv_r + Np1);          // 2 Np1: fields of R1, R3
     float2* tabB = tabA + 2 * Np1;                  // 2 Np1: fields of R2, R4
@@ -335,12 +344,14 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
     unsigned int gen = 0;
     int cyc = 0;
     int K = 0;
-    unsigned int* histA = hist;
-    unsigned int* histB = hist + hw;
+    // lane l deposits into copy l mod copies: the lanes of a warp hold
+    // phase-space neighbours, which mostly fall into the same cell
+    unsigned int* histA = hist + (lane & (copies - 1)) * 2 * hw;
+    unsigned int* histB = histA + hw;
 
     for (int k = 0;; ++k) {
         // ---- sweep A(k): finish step k-1 (write row k), sample k, deposit stage pair 1 of step k
-        for (int idx = threadIdx.x; idx < 2 * hw; idx += blockDim.x) hist[idx] = 0u;
+        for (int idx = threadIdx.x; idx < copies * 2 * hw; idx += blockDim.x) hist[idx] = 0u;
         if (threadIdx.x == 0) {
             s_cnt = 0;
             s_next = 0;
@@ -430,7 +441,7 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
         ++cyc;
 
         // ---- sweep B(k): gather pair 1 of step k, deposit stage pair 2
-        for (int idx = threadIdx.x; idx < 2 * hw; idx += blockDim.x) hist[idx] = 0u;
+        for (int idx = threadIdx.x; idx < copies * 2 * hw; idx += blockDim.x) hist[idx] = 0u;
         if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
         const float2 rq = P.rot[rot_index(P, 2ll * k + 2)];  // Phi(t_k + h)
@@ -764,7 +775,7 @@ __global__ void k_batch_status(const BeamDesc32* __restrict__ beams, int n_beams
         out[b] = *beams[b].B.status;
 }
 
-size_t window32_batch_smem(int max_cells) { return max_cells > 0 ? coop32_smem_bytes(max_cells) : 0; }
+size_t window32_batch_smem(int max_cells) { return max_cells > 0 ? coop32_smem_bytes(max_cells, 1) : 0; }
 
 cudaError_t window32_batch_attr(size_t smem) {
     return cudaFuncSetAttribute(k_window32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -860,7 +871,14 @@ __global__ void k_moments32(DevParams P, WinBufs32 B, double* part_d, long long*
 cudaError_t window32_prepare(DevParams& P, int block, int blocks_per_sm, int sm_count, long long ld,
                              WindowLaunch* L) {
     L->coop_block = block;
-    L->coop_smem = coop32_smem_bytes(P.n_cells);
+    // histogram copies: as many as fit (up to kHist32CopiesMax) while a block
+    // deposits enough positions per cycle for same-cell conflicts to matter
+    int copies = kHist32CopiesMax;
+    const long long per_block_est = P.n / (sm_count > 0 ? sm_count : 1);
+    while (copies > 1 && (coop32_smem_bytes(P.n_cells, copies) > 200 * 1024 || per_block_est < 256ll * copies * 32))
+        copies >>= 1;
+    P.hist_copies = copies;
+    L->coop_smem = coop32_smem_bytes(P.n_cells, copies);
     L->hist = 0;
     L->stage = 0;
     if (L->coop_smem > 227 * 1024) return cudaErrorNotSupported;
@@ -883,7 +901,6 @@ cudaError_t window32_prepare(DevParams& P, int block, int blocks_per_sm, int sm_
     // field and cycle
     const long long per_block = (n_groups + grid - 1) / grid * kGroup;
     if (per_block > (1ll << 21)) return cudaErrorNotSupported;
-    P.hist_copies = 1;
     return cudaSuccess;
 }
 
