@@ -348,6 +348,7 @@ typedef struct {
     int32_t block, blocks_per_sm, grid, sort_every;
     int32_t graph;                     /* 1: steps replay a captured CUDA graph     */
     int32_t graph_error;               /* cudaError_t of a failed capture, else 0   */
+    int32_t hist_copies;               /* copies of each block's charge histogram   */
     double  alloc_power;
 } pic_batch_config_t;
 
@@ -356,13 +357,16 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
 /* n_steps macro steps of every beam.  Synchronises after each step and
    returns the first non-OK device status of any beam. */
 int pic_batch_step(pic_batch* b, int64_t n_steps);
+/* hist_copies: 1, 2 or 4 copies of each block's charge histogram (lane l
+   of a warp deposits into copy l mod hist_copies); more copies take more
+   shared memory per block and may leave fewer blocks per SM. */
 int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power,
-                         int32_t sort_every);
+                         int32_t sort_every, int32_t hist_copies);
 int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
 /* Autotuner: times steps_per_trial macro steps (after one warm step) for
-   each launch shape (block size x blocks per SM x allocation power) that
-   fits, keeps the fastest, then times the sort periods 1, 4, 16 and keeps
-   the fastest.  The trial steps are real steps of the batch (their results
+   each launch shape (block size x blocks per SM x allocation power x
+   histogram copies) that fits, keeps the fastest, then times the sort
+   periods 1, 4, 16 and keeps the fastest.  The trial steps are real steps of the batch (their results
    do not depend on the shape).  *best receives the chosen configuration. */
 int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind);

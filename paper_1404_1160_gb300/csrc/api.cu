@@ -1219,7 +1219,7 @@ struct pic_batch {
     int* d_status = nullptr;
     int* h_status = nullptr;  // pinned
     std::vector<pic::BeamDesc32> desc;
-    int block = 1024, bps = 1, grid = 0, sort_every = 4;
+    int block = 1024, bps = 1, grid = 0, sort_every = 4, copies = 1;
     double alloc_power = 1.0;
     size_t smem = 0;
     int max_cells = 0;
@@ -1248,7 +1248,7 @@ cudaError_t batch_upload(pic_batch* b) {
         pic_handle* h = b->hs[i];
         pic::BeamDesc32& d = b->desc[i];
         d.P = h->dp;
-        d.P.hist_copies = 1;  // the batch's shared memory holds one histogram per field
+        d.P.hist_copies = b->copies;  // the batch's shared memory is sized for this many
         d.B = h->B32;
         d.Tin = h->prm.periods_once ? h->Tin32 : nullptr;
         d.T_known = h->prm.periods_once ? 1 : 0;
@@ -1261,14 +1261,19 @@ cudaError_t batch_upload(pic_batch* b) {
 // Blocks per beam in proportion to (its particles)^power, at least one and
 // at most what its particles fill; weight 1/4 for the analytic fields (no
 // field cycle).
-int batch_configure(pic_batch* b, int block, int bps_want, double power) {
+int batch_configure(pic_batch* b, int block, int bps_want, double power, int copies) {
     if (block < 128 || block > 1024 || (block & 31)) return PIC_ERR_INVALID_ARG;
-    if (b->smem > 0) {
-        cudaError_t e = pic::window32_batch_attr(b->smem);
+    if (copies != 1 && copies != 2 && copies != 4) return PIC_ERR_INVALID_ARG;
+    const size_t smem = pic::window32_batch_smem(b->max_cells, copies);
+    if (smem > 227 * 1024) return PIC_ERR_UNSUPPORTED;
+    if (smem > 0) {
+        // the larger of the new and the current size, so that the current
+        // configuration stays launchable if this one is refused below
+        cudaError_t e = pic::window32_batch_attr(smem > b->smem ? smem : b->smem);
         if (e != cudaSuccess) return map_cuda(e);
     }
     int bps = 0;
-    cudaError_t e = pic::window32_batch_occupancy(block, b->smem, &bps);
+    cudaError_t e = pic::window32_batch_occupancy(block, smem, &bps);
     if (e != cudaSuccess) return map_cuda(e);
     if (bps < 1) return PIC_ERR_UNSUPPORTED;
     if (bps_want > 0 && bps_want < bps) bps = bps_want;
@@ -1323,6 +1328,8 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power) {
     b->block = block;
     b->bps = bps;
     b->alloc_power = power;
+    b->copies = copies;
+    b->smem = smem;
     return map_cuda(batch_upload(b));
 }
 
@@ -1437,7 +1444,6 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
         }
     }
     if (!rc) {
-        b->smem = pic::window32_batch_smem(b->max_cells);
         cudaError_t e = cudaMalloc(&b->d_desc, sizeof(pic::BeamDesc32) * n_beams);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * n_beams);
         if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * n_beams);
@@ -1445,7 +1451,7 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
         rc = map_cuda(e);
     }
-    if (!rc) rc = batch_configure(b, 1024, 1, 1.0);
+    if (!rc) rc = batch_configure(b, 1024, 1, 1.0, 1);
     if (!rc) rc = map_cuda(cudaStreamSynchronize(b->st));
     if (rc) {
         batch_free(b);
@@ -1464,9 +1470,10 @@ int pic_batch_step(pic_batch* b, int64_t n_steps) {
     return PIC_OK;
 }
 
-int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power, int32_t sort_every) {
+int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power, int32_t sort_every,
+                         int32_t hist_copies) {
     if (!b || sort_every < 0 || !(alloc_power >= 0.0 && alloc_power <= 2.0)) return PIC_ERR_INVALID_ARG;
-    const int rc = batch_configure(b, block, blocks_per_sm, alloc_power);
+    const int rc = batch_configure(b, block, blocks_per_sm, alloc_power, hist_copies);
     if (!rc) b->sort_every = sort_every;
     return rc;
 }
@@ -1480,6 +1487,7 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out) {
     out->alloc_power = b->alloc_power;
     out->graph = b->use_graph ? 1 : 0;
     out->graph_error = (int32_t)b->graph_error;
+    out->hist_copies = b->copies;
     return PIC_OK;
 }
 
@@ -1488,8 +1496,15 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
     struct Cand {
         int block, bps;
         double power;
+        int copies;
     };
-    const Cand shapes[] = {{1024, 1, 1.0}, {1024, 1, 0.85}, {512, 2, 1.0}, {512, 2, 0.85}, {256, 4, 1.0}};
+    std::vector<Cand> shapes;
+    const Cand base[] = {{1024, 1, 1.0, 1}, {1024, 1, 0.85, 1}, {512, 2, 1.0, 1}, {512, 2, 0.85, 1}, {256, 4, 1.0, 1}};
+    for (int copies : {1, 2, 4})
+        for (Cand c : base) {
+            c.copies = copies;
+            shapes.push_back(c);
+        }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIC_ERR_CUDA;
     auto trial = [&](double* ms) -> int {
@@ -1508,7 +1523,7 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
     Cand bestc = shapes[0];
     int rc = PIC_OK;
     for (const Cand& c : shapes) {
-        int r = batch_configure(b, c.block, c.bps, c.power);
+        int r = batch_configure(b, c.block, c.bps, c.power, c.copies);
         if (r == PIC_ERR_UNSUPPORTED) continue;  // shape does not fit this batch
         if (r) {
             rc = r;
@@ -1521,7 +1536,7 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
             bestc = c;
         }
     }
-    if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power);
+    if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies);
     int best_sort = b->sort_every;
     if (!rc) {
         double best_sort_ms = 1e300;

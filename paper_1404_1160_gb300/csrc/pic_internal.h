@@ -125,7 +125,7 @@ struct BeamDesc32 {
     int coop;             // 1: Poisson (cooperative window), 0: analytic field (per particle)
     int T_known;
 };
-size_t window32_batch_smem(int max_cells);
+size_t window32_batch_smem(int max_cells, int copies);
 cudaError_t window32_batch_attr(size_t smem);
 cudaError_t window32_batch_occupancy(int block, size_t smem, int* blocks_per_sm);
 cudaError_t launch_window32_batch(const BeamDesc32* beams, int n_beams, int grid, int block, size_t smem,

@@ -775,7 +775,7 @@ __global__ void k_batch_status(const BeamDesc32* __restrict__ beams, int n_beams
         out[b] = *beams[b].B.status;
 }
 
-size_t window32_batch_smem(int max_cells) { return max_cells > 0 ? coop32_smem_bytes(max_cells, 1) : 0; }
+size_t window32_batch_smem(int max_cells, int copies) { return max_cells > 0 ? coop32_smem_bytes(max_cells, copies) : 0; }
 
 cudaError_t window32_batch_attr(size_t smem) {
     return cudaFuncSetAttribute(k_window32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -875,7 +875,7 @@ cudaError_t window32_prepare(DevParams& P, int block, int blocks_per_sm, int sm_
     // deposits enough positions per cycle for same-cell conflicts to matter
     int copies = kHist32CopiesMax;
     const long long per_block_est = P.n / (sm_count > 0 ? sm_count : 1);
-    while (copies > 1 && (coop32_smem_bytes(P.n_cells, copies) > 200 * 1024 || per_block_est < 256ll * copies * 32))
+    while (copies > 1 && (coop32_smem_bytes(P.n_cells, copies) > 200 * 1024 || per_block_est < 64ll * copies * 32))
         copies >>= 1;
     P.hist_copies = copies;
     L->coop_smem = coop32_smem_bytes(P.n_cells, copies);

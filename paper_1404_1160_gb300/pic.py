@@ -44,7 +44,7 @@ class pic_adam_t(C.Structure):
 
 class pic_batch_config_t(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grid", C.c_int32), ("sort_every", C.c_int32),
-                ("graph", C.c_int32), ("graph_error", C.c_int32), ("alloc_power", C.c_double)]
+                ("graph", C.c_int32), ("graph_error", C.c_int32), ("hist_copies", C.c_int32), ("alloc_power", C.c_double)]
 
 
 class pic_params(C.Structure):
@@ -159,7 +159,7 @@ def load() -> C.CDLL:
             "pic_step_classic": (i32, [H, i64, i32, P(d), P(i64)]),
             "pic_batch_create": (i32, [i32, P(pic_params), P(i64), P(C.c_void_p), P(C.c_void_p), vp, P(vp)]),
             "pic_batch_step": (i32, [vp, i64]),
-            "pic_batch_set_config": (i32, [vp, i32, i32, d, i32]),
+            "pic_batch_set_config": (i32, [vp, i32, i32, d, i32, i32]),
             "pic_batch_get_config": (i32, [vp, P(pic_batch_config_t)]),
             "pic_batch_tune": (i32, [vp, i32, P(pic_batch_config_t)]),
             "pic_batch_get_particles": (i32, [vp, i32, vp, vp, i32]),
@@ -488,14 +488,15 @@ def pic_batch_step(b: Batch, n_steps: int) -> None:
     _check(load().pic_batch_step(b.ptr, int(n_steps)), "pic_batch_step")
 
 
-def pic_batch_set_config(b: Batch, block: int, blocks_per_sm: int, alloc_power: float, sort_every: int) -> None:
-    _check(load().pic_batch_set_config(b.ptr, int(block), int(blocks_per_sm), float(alloc_power), int(sort_every)),
-           "pic_batch_set_config")
+def pic_batch_set_config(b: Batch, block: int, blocks_per_sm: int, alloc_power: float, sort_every: int,
+                         hist_copies: int = 1) -> None:
+    _check(load().pic_batch_set_config(b.ptr, int(block), int(blocks_per_sm), float(alloc_power), int(sort_every),
+                                       int(hist_copies)), "pic_batch_set_config")
 
 
 def _cfg_dict(c) -> dict:
     return {"block": c.block, "blocks_per_sm": c.blocks_per_sm, "grid": c.grid, "sort_every": c.sort_every,
-            "graph": c.graph, "graph_error": c.graph_error, "alloc_power": c.alloc_power}
+            "graph": c.graph, "graph_error": c.graph_error, "hist_copies": c.hist_copies, "alloc_power": c.alloc_power}
 
 
 def pic_batch_get_config(b: Batch) -> dict:

@@ -66,7 +66,8 @@ def single_runs(beams, steps):
 def test_batch_equals_single_beams_and_ignores_the_launch_shape():
     beams = make_beams()
     ref = single_runs(beams, 3)
-    shapes = [None, (512, 2, 0.85, 1), (256, 4, 1.0, 2)]
+    # (block, blocks per SM, allocation power, sort period, histogram copies)
+    shapes = [None, (512, 2, 0.85, 1, 1), (256, 4, 1.0, 2, 2), (1024, 1, 1.0, 4, 4)]
     for shape in shapes:
         b = pic.pic_batch_create([make_params(sp) for sp in SPECS], beams)
         if shape is not None:
@@ -83,12 +84,14 @@ def test_batch_equals_single_beams_and_ignores_the_launch_shape():
         cfg = pic.pic_batch_get_config(b)
         assert cfg["grid"] >= len(SPECS)
         assert cfg["graph"] == 1, cfg  # steps replay a captured graph
+        if shape is not None:
+            assert cfg["hist_copies"] == shape[4], cfg
         b.close()
 
 
 def test_autotuner_steps_are_real_steps():
     beams = make_beams()
-    ref = single_runs(beams, 1 + 5 * 3 + 3 * 3 + 2)
+    ref = single_runs(beams, 1 + 15 * 3 + 3 * 3 + 2)
     b = pic.pic_batch_create([make_params(sp) for sp in SPECS], beams)
     pic.pic_batch_step(b, 1)
     best = pic.pic_batch_tune(b, steps_per_trial=2)
@@ -98,12 +101,13 @@ def test_autotuner_steps_are_real_steps():
         R, V = pic.pic_batch_get_particles(b, i)
         assert bit_equal(R, ref[i][0]) and bit_equal(V, ref[i][1]), (best, i)
     assert best["block"] in (256, 512, 1024) and best["sort_every"] in (1, 4, 16)
+    assert best["hist_copies"] in (1, 2, 4)
     b.close()
 
 
 def ref_steps(done):
-    # the reference above ran 1 + (up to 5 shapes + 3 sort periods) x 3 + 2 steps
-    return 1 + 5 * 3 + 3 * 3 + 2 - done
+    # the reference above ran 1 + (up to 15 shapes + 3 sort periods) x 3 + 2 steps
+    return 1 + 15 * 3 + 3 * 3 + 2 - done
 
 
 def test_batch_rejects_the_fp64_path():
