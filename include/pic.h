@@ -45,7 +45,7 @@ extern "C" {
 #define PIC_ERR_CUDA          -2  /* a CUDA call failed / no usable device   */
 #define PIC_ERR_TIMEOUT       -3  /* a device-side wait hit its time limit   */
 #define PIC_ERR_OVERFLOW      -4  /* n_particles * weight_fixed >= 2^62      */
-#define PIC_ERR_UNSUPPORTED   -5  /* valid request this build does not serve */
+#define PIC_ERR_UNSUPPORTED   -5  /* valid request the library does not serve */
 #define PIC_ERR_NO_MEMORY     -6  /* device allocation failed                */
 #define PIC_ERR_TOO_LARGE     -7  /* beyond a fixed capacity (no-alloc call) */
 
