@@ -44,9 +44,9 @@ FP64_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9
 
 WORKLOADS = {
     # paper-shaped Vlasov-Poisson run (the metric's workload)
-    "vp1e6": dict(n=10**6, params=dict(), r_cut=4.0, desc="Vlasov-Poisson, eps=0.01, N_p=1e6, N_r=256 on [-4,4], CIC, dt=0.1, Lawson RK4 fine step 2*pi*eps/100, FP64"),
-    # Duffing test field, periods once at init
-    # periods once: no tracking in the window, so the storage order does not matter and the sort is off
+    "vp1e6": dict(n=10**6, params=dict(sort_every=4), r_cut=4.0, desc="Vlasov-Poisson, eps=0.01, N_p=1e6, N_r=256 on [-4,4], CIC, dt=0.1, Lawson RK4 fine step 2*pi*eps/100, FP64"),
+    # Duffing test field, periods once at init: no tracking in the window, so the storage order does not
+    # matter and the sort is off
     "duffing1e4": dict(n=10**4, params=dict(field_model=1, dt=0.05, periods_once=1, sort_every=0), r_cut=None,
                        desc="Duffing E=-r^3, eps=0.01, N_p=1e4, dt=0.05, periods once, FP64"),
     # comparator schemes (Algorithm ClassicETDAlgo) on the same beam as vp1e6

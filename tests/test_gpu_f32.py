@@ -311,3 +311,27 @@ def test_barrier_timeout_fp32():
     h = pic.pic_init(p, R0, V0)
     pic.pic_step(h, 1)
     pic.pic_destroy(h)
+
+
+@pytest.mark.slow
+def test_histogram_copies_at_scale_within_binary32_bound():
+    # The physics of the 1e8-particle workload (eps 0.001, 1024 cells,
+    # dt 0.1, sort every 4 steps) at 3e6 particles: enough per SM for the
+    # window to deposit into four histogram copies per block (lane l into
+    # copy l mod 4), few enough for the oracle to run the whole step.
+    n = 3_000_000
+    p = pic.pic_default_params(precision=1, eps=1e-3, n_cells=1024, sort_every=4)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(n, seed=11, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+    pic.pic_destroy(h)
+    Qo, no = oracle.deposit_f32(cfg, f32(R0))
+    assert np.array_equal(Q, Qo) and n_out == no
+    R, V, T, N, o, m, res, K = compare_etd(p, R0, V0, 1)
+    scale = max(1.0, float(np.max(np.hypot(res.R, res.V))))
+    bound = etd_bound(1, K, int(res.N.max()), scale)
+    er, ev = max_err(R, res.R), max_err(V, res.V)
+    print(f"3e6 particles, eps 1e-3: max err R {er:.3e} V {ev:.3e} (bound {bound:.3e})")
+    assert er <= bound and ev <= bound
+    assert m["Q_total"] + m["n_out_of_mesh"] * p.weight_fixed == n * p.weight_fixed

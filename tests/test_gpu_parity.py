@@ -365,8 +365,9 @@ def test_moments_match_numpy():
 @pytest.mark.slow
 def test_full_size_vlasov_poisson_step_matches_oracle():
     # the benchmark's workload: N_p = 1e6, eps 0.01, dt 0.1, 256 cells on
-    # [-4, 4], Lawson RK4, in the launch configuration bench.py times
-    p = pic.pic_default_params()
+    # [-4, 4], Lawson RK4, phase-space sort every 4 steps, in the launch
+    # configuration bench.py times
+    p = pic.pic_default_params(sort_every=4)
     cfg = cfg_of(p)
     R0, V0 = inputs.gaussian_beam(10**6, seed=0, r_cut=4.0)
     h = pic.pic_init(p, dev(R0), dev(V0), torch.cuda.current_stream())
