@@ -531,6 +531,38 @@ def learned_errors(prm, wl, net, out_scale):
         out[f"err_{name}_median"] = float(np.median(e))
         out[f"err_{name}_rms99"] = float(np.sqrt(np.mean(e[:int(0.99 * e.size)] ** 2)))
     out["error_sample"] = f"{lw['eval_n']} held-out particles of the same beam, one macro step, vs the fine-solver reference"
+
+    # long time: 10 macro steps (t = 10 dt) from the same held-out beam; the
+    # reference is the fine solver over the whole time on the FP64 path
+    n_long = 10
+    ref = pic.pic_init(clone(precision=0), R0, V0)
+    m0 = pic.pic_moments(ref)
+    pic.pic_fine_advance(ref, n_long * prm.dt)
+    Rf, Vf = pic.pic_get_particles(ref)
+    mf = pic.pic_moments(ref)
+    Qf = pic.pic_get_field(ref, prm.n_cells)[0].astype(np.float64)
+    pic.pic_destroy(ref)
+    ke0, kef = m0["kinetic"], mf["kinetic"]
+    longt = {"macro_steps": n_long, "time": n_long * prm.dt,
+             "reference_kinetic_drift": (kef - ke0) / ke0}
+    for name, p, how in (("plain", prm, "plain"), ("learned", prm, "learned"), ("plain_8_small", clone(dt=prm.dt / 8), "8")):
+        h = pic.pic_init(p, R0, V0)
+        if how == "plain":
+            pic.pic_step(h, n_long)
+        elif how == "learned":
+            pic.pic_step_learned(h, net, n_long, scale=tuple(out_scale), drift_tol=lw["tol"])
+        else:
+            pic.pic_step(h, 8 * n_long)
+        R, V = pic.pic_get_particles(h)
+        m = pic.pic_moments(h)
+        Q = pic.pic_get_field(h, p.n_cells)[0].astype(np.float64)
+        pic.pic_destroy(h)
+        e = np.hypot(R - Rf, V - Vf)
+        longt[f"{name}_err_median"] = float(np.median(e))
+        longt[f"{name}_kinetic_drift"] = (m["kinetic"] - ke0) / ke0
+        longt[f"{name}_kinetic_vs_reference"] = (m["kinetic"] - kef) / kef
+        longt[f"{name}_density_L1_vs_reference"] = float(np.abs(Q - Qf).sum() / Qf.sum())
+    out["long_time"] = longt
     return out
 
 
