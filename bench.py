@@ -276,15 +276,22 @@ def run_ours(args):
     r_o = torch.empty(n, dtype=torch.float64).pin_memory()
     v_o = torch.empty(n, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
+    parts = []  # host time of the three calls of each step (they synchronise)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         pic.pic_set_particles(h, r_h, v_h)
+        tb = time.perf_counter()
         do_step()
+        tc = time.perf_counter()
         pic.pic_get_particles(h, r_o, v_o)
+        parts.append((tb - ta, tc - tb, time.perf_counter() - tc))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n}
+    pm = np.mean(np.array(parts), axis=0) * 1e3
+    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n,
+           "mean_ms": {"set_particles": float(pm[0]), "step": float(pm[1]), "get_particles": float(pm[2])}}
     pic.pic_destroy(h)
 
     if rank != 0:

@@ -51,6 +51,11 @@ extern "C" {
 
 /* ---- enumerations ------------------------------------------------------ */
 enum { PIC_FIELD_POISSON = 0, PIC_FIELD_DUFFING = 1, PIC_FIELD_ZERO = 2 };
+/* Two readings of d/dr (rE) = rho (eq. VlasPoissAxSymBeam) on the signed
+   radial coordinate: EVEN takes E = (1/r) int_0^r rho as written (E is then
+   even in r, E(0) = rho(0)); ODD takes its odd extension E = rE(r)/|r|,
+   E(0) = 0, for which (R, V) -> (-R, -V) maps solutions to solutions. */
+enum { PIC_PARITY_EVEN = 0, PIC_PARITY_ODD = 1 };
 /* Fine solver of steps 1 and 3 of Algorithm ETDFSSModAlgo:
    PIC_FINE_RK4 is the paper's explicit RK4 (Remark CompOfThePeriodsRem);
    PIC_FINE_LAWSON_RK4 advances the linear part (1/eps) M y of
@@ -93,6 +98,8 @@ typedef struct {
                                   particle storage (0 = never, default 1); the
                                   public particle order never changes          */
     int64_t  wait_limit_ns;    /* limit of every device-side wait, 0 = 2 s        */
+    int32_t  field_parity;     /* PIC_PARITY_EVEN (default) or PIC_PARITY_ODD     */
+    int32_t  reserved;         /* 0                                               */
 } pic_params;
 
 /* Fills p with the defaults of the paper-shaped Vlasov-Poisson run:

@@ -60,7 +60,7 @@ class Params(C.Structure):
         ("total_charge", C.c_double),
         ("weight_fixed", C.c_uint64),
         ("max_window_steps", C.c_int32),
-        ("pad_", C.c_int32),
+        ("field_parity", C.c_int32),
     ]
 
 
@@ -95,12 +95,13 @@ class Config:
     total_charge: float = 1.0
     weight_fixed: int = 1 << 32
     max_window_steps: int = 300
+    field_parity: int = 0  # 0: E = (1/r) int_0^r rho (even); 1: its odd extension
 
     def to_c(self) -> Params:
         return Params(
             self.eps, self.dt, self.field_model, self.fine_solver, self.steps_per_turn,
             self.n_cells, self.r_min, self.r_max, self.total_charge, self.weight_fixed,
-            self.max_window_steps, 0,
+            self.max_window_steps, self.field_parity,
         )
 
 

@@ -48,6 +48,7 @@ static int check_params(const orc_params* p) {
     if (p->field_model < 0 || p->field_model > 2) return -1;
     if (p->fine_solver < 0 || p->fine_solver > 1) return -1;
     if (p->max_window_steps < 2 * p->steps_per_turn + 2) return -1;
+    if (p->field_parity != 0 && p->field_parity != 1) return -1;
     if (p->field_model == 0) {
         if (p->n_cells < 2 || (p->n_cells & 1)) return -1;
         if (!(p->r_max > 0.0) || p->r_min != -p->r_max) return -1;
@@ -155,16 +156,21 @@ int orc_poisson(const orc_params* p, int64_t n_particles, const int64_t* Q, int6
     const double q_half = 0.5 * q_unit;
     for (int64_t j = 0; j <= Nc; ++j) {
         if (j == c) {
-            /* limit r -> 0 of (1/r) * int_0^r rho = rho(0) = Q_c*q_unit/h_r */
-            E[j] = ((double)Q[c] * q_unit) * d.inv_hr;
+            /* limit r -> 0 of (1/r) * int_0^r rho = rho(0) = Q_c*q_unit/h_r;
+               the odd extension is 0 on the axis */
+            E[j] = p->field_parity ? 0.0 : ((double)Q[c] * q_unit) * d.inv_hr;
         } else {
             double r_j = p->r_min + (double)j * d.hr;
             double rE = (double)S[j] * q_half;
             E[j] = rE * (1.0 / r_j);
+            /* odd extension: rE/|r|, i.e. the sign flips left of the axis */
+            if (p->field_parity && j < c) E[j] = -E[j];
         }
     }
     if (rE_edges) {
-        rE_edges[0] = (double)S[0] * q_half;
+        /* the off-mesh gather divides the edge value by R: with the odd
+           extension the lower edge carries its sign flip (rE/|R| = -rE/R) */
+        rE_edges[0] = p->field_parity ? -((double)S[0] * q_half) : (double)S[0] * q_half;
         rE_edges[1] = (double)S[Nc] * q_half;
     }
     if (S_out) memcpy(S_out, S, (size_t)(Nc + 1) * sizeof(int64_t));

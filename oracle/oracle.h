@@ -34,7 +34,10 @@ typedef struct {
     double   total_charge;     /* sum of the particle weights                   */
     uint64_t weight_fixed;     /* W: fixed-point charge per particle, 2^k        */
     int32_t  max_window_steps; /* cap on the fine window of one macro step       */
-    int32_t  pad_;
+    int32_t  field_parity;     /* 0: E = (1/r) int_0^r rho as written (even in r);
+                                  1: the odd extension E(r) = rE(r)/|r|, E(0) = 0
+                                  (the other reading of eq. VlasPoissAxSymBeam,
+                                  for comparison)                               */
 } orc_params;
 
 typedef struct {

@@ -55,6 +55,7 @@ int check_params(const pic_params* p, bool need_mesh) {
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 32) return PIC_ERR_INVALID_ARG;
     if (p->sort_every < 0) return PIC_ERR_INVALID_ARG;
     if (p->wait_limit_ns < 0) return PIC_ERR_INVALID_ARG;
+    if (p->field_parity != PIC_PARITY_EVEN && p->field_parity != PIC_PARITY_ODD) return PIC_ERR_INVALID_ARG;
     if (need_mesh || p->field_model == PIC_FIELD_POISSON) {
         if (p->n_cells < 2 || p->n_cells > 65536 || (p->n_cells & 1)) return PIC_ERR_INVALID_ARG;
         if (!(p->r_max > 0.0) || !std::isfinite(p->r_max) || p->r_min != -p->r_max) return PIC_ERR_INVALID_ARG;
@@ -115,6 +116,7 @@ void make_devparams(const pic_params* p, long long n, DevParams* d) {
     d->n = n;
     d->wait_ns = p->wait_limit_ns > 0 ? p->wait_limit_ns : 2000000000ll;
     d->bar_extra = 0;
+    d->parity_odd = p->field_parity == PIC_PARITY_ODD ? 1 : 0;
     // FP32 form: the same constants rounded once to binary32
     d->r_min_f = (float)p->r_min;
     d->inv_hr_f = (float)d->inv_hr;

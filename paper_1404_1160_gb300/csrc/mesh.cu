@@ -194,13 +194,16 @@ __global__ void k_field_from_prefix(DevParams P, const long long* __restrict__ Q
         long long S = G[j] - Gc;
         double e;
         if (j == c) {
-            e = ((double)Q[c] * P.q_unit) * P.inv_hr;
+            e = P.parity_odd ? 0.0 : ((double)Q[c] * P.q_unit) * P.inv_hr;
         } else {
             double r = P.r_min + (double)j * P.hr;
             e = ((double)S * P.q_half) * (1.0 / r);
+            if (P.parity_odd && j < c) e = -e;  // odd reading: rE / |r|
         }
         E[j] = e;
-        if (j == 0) edges[0] = (double)S * P.q_half;
+        // the off-mesh gather divides the edge rE by R; the odd reading's
+        // lower edge carries the sign flip
+        if (j == 0) edges[0] = P.parity_odd ? -((double)S * P.q_half) : (double)S * P.q_half;
         if (j == Nc) edges[1] = (double)S * P.q_half;
     }
 }

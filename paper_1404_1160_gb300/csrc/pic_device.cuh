@@ -44,6 +44,7 @@ struct DevParams {
     long long n;                       // particles
     long long wait_ns;                 // limit of device-side waits
     int bar_extra;                     // testing only: arrivals a barrier waits for beyond the grid
+    int parity_odd;                    // 1: E = rE(r)/|r| (odd in r, 0 on the axis); 0: E = rE(r)/r
     int hist_copies;                   // copies of each block's charge histogram (window kernel)
     // FP32 form (precision 1): the same quantities rounded once to binary32
     float r_min_f, inv_hr_f, ncells_f, Wf;

@@ -95,7 +95,9 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
             sl = (ex > P.log2W + 1 && ex < 0x7ff) ? scale_pow2(d, -P.log2W) : d * P.invW;
         }
         tab[f * Np1 + j] = make_double2(e, sl);
-        if (j == 0) edges[2 * f] = i64_to_double(S) * P.q_half;
+        // the off-mesh gather divides the edge rE by R: the odd reading
+        // (rE / |R|) carries the sign flip in the lower edge value
+        if (j == 0) edges[2 * f] = P.parity_odd ? -(i64_to_double(S) * P.q_half) : i64_to_double(S) * P.q_half;
         if (j == Nc) edges[2 * f + 1] = i64_to_double(S) * P.q_half;
     };
     if (field_build_regs(P, Qg, inv_r, s_warp, emit)) {
@@ -112,10 +114,11 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
         // int64 -> double exactly as (double)S, on the integer pipe
         const double Sd = i64_to_double(S);
         double e;
-        if (j == c) e = (i64_to_double(q[f * Np1 + c]) * P.q_unit) * P.inv_hr;
+        if (j == c) e = P.parity_odd ? 0.0 : (i64_to_double(q[f * Np1 + c]) * P.q_unit) * P.inv_hr;
         else e = (Sd * P.q_half) * inv_r[j];
+        if (P.parity_odd && j < c) e = -e;
         tab[idx].x = e;
-        if (j == 0) edges[2 * f] = Sd * P.q_half;
+        if (j == 0) edges[2 * f] = P.parity_odd ? -(Sd * P.q_half) : Sd * P.q_half;
         if (j == Nc) edges[2 * f + 1] = Sd * P.q_half;
     }
     __syncthreads();

@@ -107,7 +107,8 @@ __device__ void build_fields32(const DevParams& P, const unsigned long long* Qg,
     if (stop_src && threadIdx.x == 0) *s_stop = (__ldcg(stop_src) == 0);
     auto emit = [&](int f, int j, double e, double en, long long S) {
         tab[f * Np1 + j] = make_float2((float)e, j < Nc ? (float)(en - e) : 0.0f);
-        if (j == 0) edges[2 * f] = (float)(i64_to_double(S) * P.q_half);
+        // odd reading: the lower edge value carries the sign flip (rE / |R|)
+        if (j == 0) edges[2 * f] = (float)(P.parity_odd ? -(i64_to_double(S) * P.q_half) : i64_to_double(S) * P.q_half);
         if (j == Nc) edges[2 * f + 1] = (float)(i64_to_double(S) * P.q_half);
     };
     if (field_build_regs(P, Qg, inv_r, s_warp, emit)) {
@@ -128,9 +129,10 @@ __device__ void build_fields32(const DevParams& P, const unsigned long long* Qg,
         const int f = idx >= Np1, j = idx - f * Np1;
         const double Sd = i64_to_double(g[idx] - s_c[f]);
         double ev;
-        if (j == c) ev = (i64_to_double(s_c[2 + f]) * P.q_unit) * P.inv_hr;
+        if (j == c) ev = P.parity_odd ? 0.0 : (i64_to_double(s_c[2 + f]) * P.q_unit) * P.inv_hr;
         else ev = (Sd * P.q_half) * inv_r[j];
-        if (j == 0) edges[2 * f] = (float)(Sd * P.q_half);
+        if (P.parity_odd && j < c) ev = -ev;
+        if (j == 0) edges[2 * f] = (float)(P.parity_odd ? -(Sd * P.q_half) : Sd * P.q_half);
         if (j == Nc) edges[2 * f + 1] = (float)(Sd * P.q_half);
         e[idx] = ev;
     }

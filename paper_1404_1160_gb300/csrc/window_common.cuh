@@ -70,7 +70,8 @@ static __device__ void block_exscan_pairs2(const long long* q, long long* g, int
 // the exact trapezoid sums g_j = sum_{m<j} (q_m + q_{m+1}) are a warp scan
 // plus the totals of the preceding warps (s_tot), S_j = g_j - g_c, and
 //   E_j = (S_j q_unit/2) (1/r_j),  E_c = (q_c q_unit) (1/h_r),
-// the same operations in the same order as the staged build.  Each owned
+// the same operations in the same order as the staged build (with the odd
+// reading, E_j = -E_j left of the axis and E_c = 0).  Each owned
 // node is passed to emit(f, j, E_j, E_{j+1}, S_j) (E_{j+1} unused at
 // j = n_cells).  Covers n_cells + 1 <= 31 R (blockDim/64) nodes; returns
 // false (doing nothing) when R = 4 would not suffice.  s_tot: 64 int64.
@@ -111,8 +112,9 @@ static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, co
     const long long gc = s_tot[f * 32 + 16];
     auto field_at = [&](int j, long long S, long long qj) -> double {
         if (j > Nc) return 0.0;
-        if (j == c) return (i64_to_double(qj) * P.q_unit) * P.inv_hr;
-        return (i64_to_double(S) * P.q_half) * inv_r[j];
+        if (j == c) return P.parity_odd ? 0.0 : (i64_to_double(qj) * P.q_unit) * P.inv_hr;
+        const double e = (i64_to_double(S) * P.q_half) * inv_r[j];
+        return (P.parity_odd && j < c) ? -e : e;  // odd reading: rE / |r|
     };
     long long S = g0 - gc;
     double Ecur = field_at(j0, S, q[0]);

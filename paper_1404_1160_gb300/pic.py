@@ -28,6 +28,7 @@ PIC_ERR_NO_MEMORY = -6
 PIC_ERR_TOO_LARGE = -7
 
 PIC_FIELD_POISSON, PIC_FIELD_DUFFING, PIC_FIELD_ZERO = 0, 1, 2
+PIC_PARITY_EVEN, PIC_PARITY_ODD = 0, 1
 PIC_FINE_RK4, PIC_FINE_LAWSON_RK4 = 0, 1
 PIC_PTR_HOST, PIC_PTR_DEVICE = 0, 1
 
@@ -66,6 +67,8 @@ class pic_params(C.Structure):
         ("blocks_per_sm", C.c_int32),
         ("sort_every", C.c_int32),
         ("wait_limit_ns", C.c_int64),
+        ("field_parity", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 

@@ -12,7 +12,7 @@ def cfg_of(p) -> "oracle.Config":
     return oracle.Config(eps=p.eps, dt=p.dt, field_model=p.field_model, fine_solver=p.fine_solver,
                          steps_per_turn=p.steps_per_turn, n_cells=p.n_cells, r_min=p.r_min, r_max=p.r_max,
                          total_charge=p.total_charge, weight_fixed=p.weight_fixed,
-                         max_window_steps=p.max_window_steps)
+                         max_window_steps=p.max_window_steps, field_parity=p.field_parity)
 
 
 def assert_close(gpu, ref, rtol=STATE_RTOL, what=""):

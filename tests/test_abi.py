@@ -60,6 +60,7 @@ def test_host_only_entry_points(lib):
     p = pic.pic_default_params()
     assert (p.eps, p.dt, p.n_cells, p.steps_per_turn, p.r_max) == (0.01, 0.1, 256, 100, 4.0)
     assert p.weight_fixed == 1 << 32 and p.max_window_steps == 300
+    assert p.field_parity == pic.PIC_PARITY_EVEN
     assert pic.pic_strerror(pic.PIC_ERR_TIMEOUT).startswith("device-side wait")
 
 
@@ -68,8 +69,8 @@ def test_struct_layout_matches_header(lib):
 
     from paper_1404_1160_gb300 import pic
 
-    # pic_params: 2 doubles, 4 int32, 3 doubles, uint64, 6 int32, int64
-    assert ctypes.sizeof(pic.pic_params) == 2 * 8 + 4 * 4 + 3 * 8 + 8 + 6 * 4 + 8
+    # pic_params: 2 doubles, 4 int32, 3 doubles, uint64, 6 int32, int64, 2 int32
+    assert ctypes.sizeof(pic.pic_params) == 2 * 8 + 4 * 4 + 3 * 8 + 8 + 6 * 4 + 8 + 2 * 4
     assert ctypes.sizeof(pic.pic_moments_t) == 21 * 8
 
 
@@ -87,7 +88,8 @@ def test_bad_arguments_rejected_without_device(lib):
     for kw, rc in (({"precision": 1, "fine_solver": pic.PIC_FINE_RK4}, pic.PIC_ERR_UNSUPPORTED),
                    ({"precision": 1, "weight_fixed": 1 << 33}, pic.PIC_ERR_UNSUPPORTED),
                    ({"precision": 1, "dt": 1e5}, pic.PIC_ERR_UNSUPPORTED),
-                   ({"precision": 2}, pic.PIC_ERR_INVALID_ARG)):
+                   ({"precision": 2}, pic.PIC_ERR_INVALID_ARG),
+                   ({"field_parity": 2}, pic.PIC_ERR_INVALID_ARG)):
         with pytest.raises(pic.PicError) as ei:
             pic.pic_init(pic.pic_default_params(**kw), np.zeros(4), np.zeros(4))
         assert ei.value.status == rc

@@ -335,3 +335,19 @@ def test_histogram_copies_at_scale_within_binary32_bound():
     print(f"3e6 particles, eps 1e-3: max err R {er:.3e} V {ev:.3e} (bound {bound:.3e})")
     assert er <= bound and ev <= bound
     assert m["Q_total"] + m["n_out_of_mesh"] * p.weight_fixed == n * p.weight_fixed
+
+
+def test_odd_field_reading_within_binary32_bound():
+    p = pic.pic_default_params(precision=1, field_parity=pic.PIC_PARITY_ODD)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(8001, seed=9, r_cut=4.5)
+    h = pic.pic_init(p, R0, V0)
+    Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+    pic.pic_destroy(h)
+    Qo, no = oracle.deposit_f32(cfg, f32(R0))
+    _, Eo, edges_o = oracle.poisson(cfg, Qo, R0.size)
+    assert np.array_equal(Q, Qo) and bit_equal(E, Eo) and bit_equal(edges, edges_o)
+    R, V, T, N, o, m, res, K = compare_etd(p, R0, V0, 2)
+    scale = max(1.0, float(np.max(np.hypot(res.R, res.V))))
+    bound = etd_bound(2, K, int(res.N.max()), scale)
+    assert max_err(R, res.R) <= bound and max_err(V, res.V) <= bound

@@ -149,6 +149,32 @@ def test_etd_step_poisson_matches_oracle(solver, n):
     pic.pic_destroy(h)
 
 
+@pytest.mark.parametrize("solver", [pic.PIC_FINE_RK4, pic.PIC_FINE_LAWSON_RK4])
+@pytest.mark.parametrize("n_cells,r_cut", [(256, 4.0), (100, 4.5)])
+def test_odd_field_reading_matches_oracle(solver, n_cells, r_cut):
+    # the odd extension E = rE/|r| (E = 0 on the axis) in every field cycle of
+    # the window, in the standalone field and in the off-mesh gather (r_cut
+    # 4.5 puts particles beyond the mesh on both sides; 100 cells is not a
+    # power of two)
+    p = pic.pic_default_params(fine_solver=solver, n_cells=n_cells, field_parity=pic.PIC_PARITY_ODD)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(6001, seed=8, r_cut=r_cut)
+    h = pic.pic_init(p, R0, V0)
+    Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+    Qo, no = oracle.deposit(cfg, R0)
+    _, Eo, edges_o = oracle.poisson(cfg, Qo, R0.size)
+    assert np.array_equal(Q, Qo) and n_out == no
+    assert bit_equal(E, Eo) and bit_equal(edges, edges_o) and E[n_cells // 2] == 0.0
+    Ro, Vo = R0, V0
+    for step in range(2):
+        pic.pic_step(h, 1)
+        res = oracle.etd_step(cfg, Ro, Vo)
+        Ro, Vo = res.R, res.V
+        R, V = pic.pic_get_particles(h)
+        assert bit_equal(R, Ro) and bit_equal(V, Vo), step
+    pic.pic_destroy(h)
+
+
 @pytest.mark.parametrize("W_log2", [20, 40])
 def test_etd_step_with_other_fixed_point_weights(W_log2):
     # W = 2^40: right weights floor(f W) above 2^32 (the 64-bit histogram);

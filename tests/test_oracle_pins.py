@@ -286,6 +286,48 @@ def test_poisson_uniform_rho_gives_constant_E():
     assert edges[1] == pytest.approx(E[256] * 4.0, rel=1e-15)
 
 
+def test_poisson_odd_reading_uniform_rho_gives_signed_constant():
+    # the odd extension of the same field: E(r) = rE(r)/|r| = rho0 sign(r)
+    # inside the charge, 0 on the axis; outside, rE/|r| keeps the edge value
+    c = pcfg(field_parity=1)
+    Q = np.zeros(257, np.int64)
+    Q[128 - 40:128 + 41] = 1 << 33
+    n_p = 1000
+    S, E, edges = oracle.poisson(c, Q, n_p)
+    q_unit = 1.0 / (n_p * c.weight_fixed)
+    rho0 = (1 << 33) * q_unit / (8 / 256)
+    r = -4 + np.arange(257) / 32
+    assert E[128] == 0.0
+    assert np.allclose(E[128 + 1:128 + 41], rho0, rtol=1e-15, atol=0)
+    assert np.allclose(E[128 - 40:128], -rho0, rtol=1e-15, atol=0)
+    assert np.allclose((E * np.abs(r))[128 + 41:], (E * r)[128 + 41], rtol=1e-14)
+    # the same integer sums as the literal reading; the field differs only by
+    # the sign left of the axis and by its value on the axis
+    S0, E0, edges0 = oracle.poisson(pcfg(), Q, n_p)
+    assert np.array_equal(S, S0)
+    assert np.array_equal(E[129:], E0[129:]) and np.array_equal(E[:128], -E0[:128])
+    assert edges[0] == -edges0[0] and edges[1] == edges0[1]
+    # off the mesh below: rE_edge / |R|
+    e = oracle.gather(c, np.array([-5.0, 5.0]), E, edges)
+    assert e[0] == pytest.approx(edges0[0] / 5.0, rel=1e-15) and e[1] == pytest.approx(edges0[1] / 5.0, rel=1e-15)
+
+
+def test_odd_reading_is_mirror_equivariant_and_the_literal_one_is_not():
+    # with E odd in r, (R, V) -> (-R, -V) maps solutions to solutions, so one
+    # macro step of the mirrored beam is the mirror of the step (up to the
+    # fixed-point deposit, which rounds f W down on both sides: one unit of
+    # W per particle); with the literal (even) field it is not
+    R0, V0 = inputs.gaussian_beam(400, seed=5, r_cut=3.5)
+    diffs = {}
+    for parity in (0, 1):
+        c = pcfg(field_parity=parity, dt=0.1)
+        a = oracle.etd_step(c, R0, V0)
+        b = oracle.etd_step(c, -R0, -V0)
+        diffs[parity] = max(np.max(np.abs(a.R + b.R)), np.max(np.abs(a.V + b.V)))
+    assert diffs[1] < 1e-11, diffs
+    assert diffs[0] > 1e-4, diffs
+
+
 def test_poisson_linear_rho_gives_half_slope():
     # rho = a + b |r| => rE = a r + b r|r|/2 => E = a + b |r|/2 (trapezoid is
     # exact on each side since rho is linear there)
