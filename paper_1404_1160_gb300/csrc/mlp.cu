@@ -490,10 +490,14 @@ __global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedA
         Tile T;
         tile_forward(S, x, T);
         if (t < 2) {
+            // row g (t = 0) or g + 8 (t = 1); selects rather than T.out[t]:
+            // an index that depends on the lane would move the tile to local memory
             const int h = t;
             const long long s = tile * 16 + g + 8 * h;
-            const double dR = (double)(A.scale_R * T.out[h][0]), dV = (double)(A.scale_V * T.out[h][1]);
-            if (valid[h] && (dR != 0.0 || dV != 0.0)) {
+            const float o0 = h ? T.out[1][0] : T.out[0][0], o1 = h ? T.out[1][1] : T.out[0][1];
+            const bool ok = h ? valid[1] : valid[0];
+            const double dR = (double)(A.scale_R * o0), dV = (double)(A.scale_V * o1);
+            if (ok && (dR != 0.0 || dV != 0.0)) {
                 double Rp, Vp, Rl, Vl;
                 if (PREC == 0) {
                     const double2 pl = ((const double2*)A.y)[s];
@@ -633,10 +637,13 @@ cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_
     if (A.n == 0) return cudaSuccess;
     const long long tiles = (A.n + 15) / 16;
     long long g = (tiles + 3) / 4;
-    const long long cap = (long long)sm_count * 8;
+    // one wave: as many blocks as are resident at once (the kernel strides over the tiles)
+    auto fn = A.prec == 0 ? k_learned_apply<0> : k_learned_apply<1>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFbThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long cap = (long long)sm_count * per_sm;
     const int grid = (int)(g < 1 ? 1 : (g < cap ? g : cap));
-    if (A.prec == 0) k_learned_apply<0><<<grid, kFbThreads, 0, st>>>(m->D, A);
-    else k_learned_apply<1><<<grid, kFbThreads, 0, st>>>(m->D, A);
+    fn<<<grid, kFbThreads, 0, st>>>(m->D, A);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
