@@ -128,8 +128,8 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
    interpolation of the fine solution (Remark QuadraticInterpolationRem);
    (4) y^{n+1} = y(o) + N (y(o+T) - y(o)) (eq. MainFormula1).  With the
    Poisson model every fine stage is a full field cycle of all particles:
-   deposit, trapezoid integral, gather (Sec. 3: all particles pushed far
-   enough "to calculate the correct self-consistent electric field").
+   deposit, trapezoid integral, gather (Sec. 3: every particle is advanced
+   through the whole window, since the self-consistent field needs them all).
    Synchronises the stream and returns the device status of the run. */
 int pic_step(pic_handle* h, int64_t n_steps);
 

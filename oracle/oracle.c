@@ -9,7 +9,7 @@
  *  - Rounding.  Every update of the form y + a*k is evaluated with one
  *    rounding (C99 fma); every other expression is evaluated left to right
  *    exactly as written, with floating-point contraction off at compile time.
- *  - Field (Sec. 2.3, "trapezoidal formula ... 256 cells"): the mesh has
+ *  - Field (Sec. 2.3: trapezoid rule on a radial mesh of 256 cells): the mesh has
  *    nodes r_j = r_min + j*h_r, j = 0..n_cells, and the node c = n_cells/2 is
  *    r = 0.  Charge is deposited by linear (cloud-in-cell) weights as exact
  *    integers (W units per particle), the trapezoid integral of

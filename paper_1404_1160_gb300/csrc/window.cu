@@ -5,8 +5,9 @@
 //
 // Self-consistent Poisson field: one cooperative persistent launch per macro
 // step.  Each fine stage needs the field of every particle's stage position
-// (Sec. 3: all particles are pushed far enough "to calculate the correct
-// self-consistent electric field").  Because E enters only dV/dt, the
+// (Sec. 3: the window advances every particle, not only those still
+// looking for their period, because the self-consistent field needs them
+// all).  Because E enters only dV/dt, the
 // R-component of stage s depends on fields of stages <= s-2, so stages pair
 // up: RK4 deposits stages (1,2) then (3,4); Lawson RK4 deposits (1,3) then
 // (2,4).  One fine step is therefore two field cycles:
