@@ -351,3 +351,15 @@ def test_odd_field_reading_within_binary32_bound():
     scale = max(1.0, float(np.max(np.hypot(res.R, res.V))))
     bound = etd_bound(2, K, int(res.N.max()), scale)
     assert max_err(R, res.R) <= bound and max_err(V, res.V) <= bound
+
+
+@pytest.mark.parametrize("n_cells,block", [(800, 512), (2048, 1024)])
+def test_fp32_field_build_node_counts_per_thread(n_cells, block):
+    # 4 nodes per thread in the register field build (800 cells, 512-thread
+    # blocks) and the staged build (2048 cells), within the binary32 bound
+    p = pic.pic_default_params(precision=1, n_cells=n_cells, block_size=block)
+    R0, V0 = inputs.gaussian_beam(30_000, seed=13, r_cut=4.0)
+    R, V, T, N, o, m, res, K = compare_etd(p, R0, V0, 1)
+    scale = max(1.0, float(np.max(np.hypot(res.R, res.V))))
+    bound = etd_bound(1, K, int(res.N.max()), scale)
+    assert max_err(R, res.R) <= bound and max_err(V, res.V) <= bound

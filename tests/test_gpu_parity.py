@@ -175,6 +175,22 @@ def test_odd_field_reading_matches_oracle(solver, n_cells, r_cut):
     pic.pic_destroy(h)
 
 
+@pytest.mark.parametrize("n_cells,block", [(800, 512), (400, 256), (2048, 1024)])
+def test_field_build_node_counts_per_thread(n_cells, block):
+    # the register field build gives each thread up to 4 nodes (800 cells on
+    # 512-thread blocks, 400 on 256: 4 nodes; 2048 on 1024: too many, the
+    # staged build); every case bit-exact against the oracle
+    p = pic.pic_default_params(n_cells=n_cells, block_size=block)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(30_000, seed=12, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 1)
+    R, V = pic.pic_get_particles(h)
+    pic.pic_destroy(h)
+    res = oracle.etd_step(cfg, R0, V0)
+    assert bit_equal(R, res.R) and bit_equal(V, res.V)
+
+
 @pytest.mark.parametrize("W_log2", [20, 40])
 def test_etd_step_with_other_fixed_point_weights(W_log2):
     # W = 2^40: right weights floor(f W) above 2^32 (the 64-bit histogram);
