@@ -282,6 +282,20 @@ int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, const int64_t*
 int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double* E_dev,
                const double* rE_edges_dev, double* e_dev, void* stream);
 
+/* Potential of the frozen field that the learned stepper's energy check uses
+   (pic_step_learned, step 4): psi(R) = int_0^R E(s) ds, psi(0) = 0, of the
+   field a particle feels.  Poisson model: E_dev (n_cells+1) and rE_edges_dev
+   (2) as pic_poisson writes them; E is the linear gather of the node values
+   inside the mesh (psi is quadratic in each cell; at the nodes it is the
+   trapezoid sum of the node field from r = 0, written to psi_nodes_dev,
+   n_cells+1) and rE_edge / r beyond an edge (psi grows like rE_edge ln r
+   there).  Duffing model (eq. RappelForce): psi = -R^4/4; zero field: 0
+   (E_dev, rE_edges_dev and psi_nodes_dev may then be NULL).  Writes
+   psi_dev[i] = psi(R_dev[i]) for n positions.  Device pointers; enqueues on
+   `stream` without synchronising. */
+int pic_frozen_potential(const pic_params* p, const double* E_dev, const double* rE_edges_dev, double* psi_nodes_dev,
+                         int64_t n, const double* R_dev, double* psi_dev, void* stream);
+
 /* ---- learned stepper ----------------------------------------------------- */
 /* The paper has no learned component: this network is an addition that
    corrects one improved-ETD macro step (Algorithm ETDFSSModAlgo) taken with a
@@ -320,6 +334,14 @@ int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_
    `steps` floats, may be NULL) receives each batch loss.  Synchronises. */
 int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T_dev, int64_t batch, int64_t steps,
                   const pic_adam_t* opt, uint64_t seed, float* loss_hist);
+/* One Adam step (Kingma & Ba, Algorithm 1) of the master weights with a
+   caller-supplied gradient grad (PIC_MLP_PARAMS floats, host or device per
+   ptr_kind), in binary32: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+   w -= lr (m c1) / (sqrt(v c2) + eps) with c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+   and t the network's Adam step count (pic_mlp_train's steps included; reset
+   by pic_mlp_set_weights); then the bfloat16 copies are refreshed.  The same
+   update kernel as pic_mlp_train.  Synchronises. */
+int pic_mlp_apply_gradient(pic_mlp* m, const float* grad, int ptr_kind, const pic_adam_t* opt);
 void pic_mlp_destroy(pic_mlp* m);
 
 /* n_steps macro steps of the learned stepper on a handle.  Each step:

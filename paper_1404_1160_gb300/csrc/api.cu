@@ -1184,6 +1184,38 @@ int pic_gather(const pic_params* p, int64_t n, const double* R_dev, const double
     return map_cuda(pic::launch_gather(d, R_dev, n, E_dev, rE_edges_dev, e_dev, (cudaStream_t)stream, sms, nullptr));
 }
 
+int pic_frozen_potential(const pic_params* p, const double* E_dev, const double* rE_edges_dev, double* psi_nodes_dev,
+                         int64_t n, const double* R_dev, double* psi_dev, void* stream) {
+    int rc = check_params(p, false);
+    if (rc) return rc;
+    const bool poisson = p->field_model == PIC_FIELD_POISSON;
+    if (n < 0 || (n > 0 && (!R_dev || !psi_dev))) return PIC_ERR_INVALID_ARG;
+    if (poisson && (!E_dev || !rE_edges_dev || !psi_nodes_dev)) return PIC_ERR_INVALID_ARG;
+    int sms = 0;
+    if ((rc = current_sm_count(&sms))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    pic::LearnedArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.n = n;
+    A.field = p->field_model;
+    A.eps = p->eps;
+    cudaError_t e = cudaSuccess;
+    if (poisson) {
+        DevParams d;
+        make_devparams(p, 1, &d);
+        e = pic::launch_psi_nodes(E_dev, d.n_cells, d.hr, psi_nodes_dev, st, nullptr);
+        A.E = E_dev;
+        A.psi = psi_nodes_dev;
+        A.edges = rE_edges_dev;
+        A.r_min = d.r_min;
+        A.hr = d.hr;
+        A.inv_hr = d.inv_hr;
+        A.n_cells = d.n_cells;
+    }
+    if (e == cudaSuccess) e = pic::launch_psi_eval(A, R_dev, psi_dev, sms, st);
+    return map_cuda(e);
+}
+
 // Testing hook: a Poisson window whose grid barrier waits for one arrival
 // that never comes, with the given limit; returns the status pic_step gives.
 int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* stream) {

@@ -411,6 +411,9 @@ extern "C" int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, con
     static std::mutex mu;
     static void* scratch_addr[256] = {};
     if (!p) return PIC_ERR_INVALID_ARG;
+    // a mesh too small for the layout arithmetic below is a bad argument
+    // (the full parameter check runs in the shared body)
+    if (p->n_cells < 2) return PIC_ERR_INVALID_ARG;
     if (p->n_cells > pic::kNoAllocMaxCells) return PIC_ERR_TOO_LARGE;
     if (n_particles <= 0 || !Q_dev || !E_dev || !rE_edges_dev) return PIC_ERR_INVALID_ARG;
     int dev = 0;

@@ -545,6 +545,20 @@ cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* ps
     return cudaGetLastError();
 }
 
+// psi at n positions: the same psi_at the energy check of k_learned_apply uses.
+__global__ void k_psi_eval(LearnedArgs A, const double* __restrict__ R, double* __restrict__ out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) out[i] = psi_at(A, R[i]);
+}
+
+cudaError_t launch_psi_eval(const LearnedArgs& A, const double* R, double* out, int sm_count, cudaStream_t st) {
+    if (A.n == 0) return cudaSuccess;
+    const long long want = (A.n + 255) / 256;
+    const int grid = (int)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
+    k_psi_eval<<<grid, 256, 0, st>>>(A, R, out);
+    return cudaGetLastError();
+}
+
 }  // namespace pic
 
 // ------------------------------------------------------------ C ABI
@@ -770,6 +784,34 @@ int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T
             if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
             if (e == cudaSuccess) loss_hist[s] = *m->loss_host;
         }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    return mlp_map(e);
+}
+
+int pic_mlp_apply_gradient(pic_mlp* m, const float* grad, int ptr_kind, const pic_adam_t* opt) {
+    if (!m || !grad || !opt || (ptr_kind != PIC_PTR_HOST && ptr_kind != PIC_PTR_DEVICE)) return PIC_ERR_INVALID_ARG;
+    if (!(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) ||
+        !(opt->eps > 0.f))
+        return PIC_ERR_INVALID_ARG;
+    // the caller's gradient as the one partial the update kernel sums
+    cudaError_t e = cudaMemcpyAsync(m->D.grad_part, grad, sizeof(float) * pic::kMParams,
+                                    ptr_kind == PIC_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->st);
+    if (e == cudaSuccess) {
+        pic::AdamArgs A;
+        std::memset(&A, 0, sizeof(A));
+        m->t += 1;
+        A.lr = opt->lr;
+        A.beta1 = opt->beta1;
+        A.beta2 = opt->beta2;
+        A.eps = opt->eps;
+        A.c1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)m->t)));
+        A.c2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)m->t)));
+        A.apply = 1;
+        const int gp = (pic::kMParams + 255) / 256;
+        pic::k_mlp_update<<<gp, 256, 0, m->st>>>(m->D, 1, 0, A);
+        pic::k_mlp_refresh<<<gp, 256, 0, m->st>>>(m->D);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
     return mlp_map(e);

@@ -224,6 +224,8 @@ cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_
 // psi at the nodes from E at the nodes (trapezoid of the piecewise-linear field).
 cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* psi, cudaStream_t st,
                              long long* launches);
+// psi at A.n positions R (the energy check's potential), written to out.
+cudaError_t launch_psi_eval(const LearnedArgs& A, const double* R, double* out, int sm_count, cudaStream_t st);
 }  // namespace pic
 
 namespace pic {

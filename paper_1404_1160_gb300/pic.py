@@ -148,6 +148,7 @@ def load() -> C.CDLL:
             "pic_poisson": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_poisson_noalloc": (i32, [P(pic_params), i64, vp, vp, vp, vp]),
             "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
+            "pic_frozen_potential": (i32, [P(pic_params), vp, vp, vp, i64, vp, vp, vp]),
             "pic_test_barrier_timeout": (i32, [i64, i32, vp]),
             "pic_mlp_num_params": (i32, []),
             "pic_mlp_create": (i32, [i64, vp, P(vp)]),
@@ -156,6 +157,7 @@ def load() -> C.CDLL:
             "pic_mlp_forward": (i32, [vp, i64, vp, vp]),
             "pic_mlp_gradients": (i32, [vp, i64, vp, vp, vp, vp, i32]),
             "pic_mlp_train": (i32, [vp, i64, vp, vp, i64, i64, P(pic_adam_t), C.c_uint64, vp]),
+            "pic_mlp_apply_gradient": (i32, [vp, vp, i32, P(pic_adam_t)]),
             "pic_mlp_destroy": (None, [vp]),
             "pic_step_learned": (i32, [H, vp, i64, C.c_float, C.c_float, d, P(i64)]),
             "pic_fine_advance": (i32, [H, d]),
@@ -370,6 +372,13 @@ def pic_gather(params: pic_params, R_dev, E_dev, edges_dev, e_dev, stream=None) 
     _check(load().pic_gather(C.byref(params), int(R_dev.numel()), _ptr(R_dev)[0], _ptr(E_dev)[0], _ptr(edges_dev)[0], _ptr(e_dev)[0], _stream(stream)), "pic_gather")
 
 
+def pic_frozen_potential(params: pic_params, E_dev, edges_dev, psi_nodes_dev, R_dev, psi_dev, stream=None) -> None:
+    """psi(R) of the frozen field (psi' = E, psi(0) = 0) at R_dev into psi_dev; node values into psi_nodes_dev."""
+    _check(load().pic_frozen_potential(C.byref(params), _ptr(E_dev)[0], _ptr(edges_dev)[0], _ptr(psi_nodes_dev)[0],
+                                       int(R_dev.numel()), _ptr(R_dev)[0], _ptr(psi_dev)[0], _stream(stream)),
+           "pic_frozen_potential")
+
+
 def pic_test_barrier_timeout(wait_limit_ns: int, stream=None, precision: int = 0) -> int:
     """Returns the raw status (PIC_ERR_TIMEOUT expected)."""
     return int(load().pic_test_barrier_timeout(wait_limit_ns, precision, _stream(stream)))
@@ -437,6 +446,14 @@ def pic_mlp_train(m: Mlp, X_dev, T_dev, batch: int, steps: int, lr=1e-3, beta1=0
     _check(load().pic_mlp_train(m.ptr, int(X_dev.shape[0]), _ptr(X_dev)[0], _ptr(T_dev)[0], int(batch), int(steps),
                                 C.byref(opt), C.c_uint64(seed), hist.ctypes.data), "pic_mlp_train")
     return hist[:int(steps)]
+
+
+def pic_mlp_apply_gradient(m: Mlp, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+    """One Adam step of the master weights with the given gradient (PIC_MLP_PARAMS floats)."""
+    g = np.ascontiguousarray(grad, dtype=np.float32)
+    assert g.size == PIC_MLP_PARAMS
+    opt = pic_adam_t(lr, beta1, beta2, eps)
+    _check(load().pic_mlp_apply_gradient(m.ptr, g.ctypes.data, PIC_PTR_HOST, C.byref(opt)), "pic_mlp_apply_gradient")
 
 
 def pic_step_learned(h: Handle, m: Mlp, n_steps: int, scale=(1.0, 1.0), drift_tol: float = 1e-4) -> int:

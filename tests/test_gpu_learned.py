@@ -201,3 +201,220 @@ def test_trained_network_gains_on_the_gaussian_beam():
     for h in (plain, lrn):
         pic.pic_destroy(h)
     m.close()
+
+
+# ---------------------------------------------------------------- oracle parity of the learned step's physics
+
+from oracle import learned as OL  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+
+
+def _dev(a, dtype=None):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda() if dtype is None else torch.from_numpy(
+        np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+@pytest.mark.parametrize("field,parity,n_cells", [(pic.PIC_FIELD_POISSON, 0, 256), (pic.PIC_FIELD_POISSON, 1, 256),
+                                                  (pic.PIC_FIELD_POISSON, 0, 100), (pic.PIC_FIELD_DUFFING, 0, 256),
+                                                  (pic.PIC_FIELD_ZERO, 0, 256)])
+def test_frozen_potential_matches_oracle(field, parity, n_cells):
+    # psi of the field of a beam on [-2, 2] with particles beyond both edges
+    # (the log branch), on nodes, on the axis and on the mesh edges
+    p = pic.pic_default_params(field_model=field, field_parity=parity, n_cells=n_cells, r_min=-2.0, r_max=2.0)
+    c = cfg_of(p)
+    R0, _ = inputs.gaussian_beam(30_000, seed=11)
+    R = np.concatenate([R0, [-2.0, 2.0, 0.0, -7.5, 12.0, np.nextafter(-2.0, -3.0), -2.0 + 4.0 / n_cells]])
+    n = R.size
+    Rd = _dev(R)
+    psi = torch.empty(n, dtype=torch.float64, device="cuda")
+    if field == pic.PIC_FIELD_POISSON:
+        Q = torch.empty(n_cells + 1, dtype=torch.int64, device="cuda")
+        nout = torch.empty(1, dtype=torch.int64, device="cuda")
+        E = torch.empty(n_cells + 1, dtype=torch.float64, device="cuda")
+        edges = torch.empty(2, dtype=torch.float64, device="cuda")
+        psi_n = torch.empty(n_cells + 1, dtype=torch.float64, device="cuda")
+        pic.pic_deposit(p, Rd, Q, nout)
+        pic.pic_poisson(p, n, Q, E, edges)
+        pic.pic_frozen_potential(p, E, edges, psi_n, Rd, psi)
+        torch.cuda.synchronize()
+        Eo, edo = OL.mesh_field(c, R)
+        assert bit_equal(E.cpu().numpy(), Eo) and bit_equal(edges.cpu().numpy(), edo)
+        pn = OL.node_potential(c, Eo)
+        scale = float(np.abs(pn).max())
+        assert np.max(np.abs(psi_n.cpu().numpy() - pn)) <= 1e-12 * scale
+    else:
+        pic.pic_frozen_potential(p, None, None, None, Rd, psi)
+        torch.cuda.synchronize()
+        Eo = edo = None
+        scale = 1.0
+    po = OL.frozen_potential(c, R, Eo, edo)
+    err = np.abs(psi.cpu().numpy() - po)
+    assert np.all(err <= 1e-12 * (scale + np.abs(po))), float(err.max())
+
+
+def _constant_net(c_R, c_V):
+    w = np.zeros(omlp.N_PARAMS, np.float32)
+    w[B3_OFF:B3_OFF + 2] = (c_R, c_V)
+    m = pic.pic_mlp_create(16)
+    pic.pic_mlp_set_weights(m, w)
+    return m, w
+
+
+def _oracle_certainty(c, plain, dR_lo, dR_hi, dV_lo, dV_hi, tol, E, edges):
+    """Per particle: (certain keep, certain fallback) of the energy check over
+    every correction in the box [dR_lo, dR_hi] x [dV_lo, dV_hi], with a
+    margin for the rounding of H on either side (1e-10 of |H| + eps max|psi|)."""
+    H0 = OL.frozen_energy(c, plain.R, plain.V, E, edges)
+    psi_scale = float(np.abs(OL.node_potential(c, E)).max()) if E is not None else 0.0
+    amb = 1e-10 * (np.abs(H0) + c.eps * psi_scale + 1e-300)
+    ms = []
+    for dR in (dR_lo, dR_hi):
+        for dV in (dV_lo, dV_hi):
+            ms.append(OL.learned_apply(c, plain.R, plain.V, dR, dV, tol, E, edges)[3])
+    ms = np.array(ms)
+    return np.all(ms < -amb, axis=0), np.all(ms > amb, axis=0)
+
+
+@pytest.mark.parametrize("parity,sort_every", [(0, 1), (1, 1), (0, 0)])
+def test_learned_step_constant_correction_matches_oracle_on_poisson(parity, sort_every):
+    # a constant correction (W3 = 0, b3 = (c_R, c_V): the network's output is
+    # b3 exactly on both sides) on a Poisson field with particles off the
+    # mesh: the keep/fallback decisions and the states equal the oracle's
+    # bit for bit wherever the decision is not within rounding of the limit
+    p = pic.pic_default_params(dt=0.4, r_min=-2.0, r_max=2.0, field_parity=parity, sort_every=sort_every)
+    c = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(20_001, seed=21)
+    scale, tol = (2.0 ** -9, 2.0 ** -10), 2e-3
+    m, w = _constant_net(1.0, -0.75)
+    h = pic.pic_init(p, R0, V0)
+    n_fb = pic.pic_step_learned(h, m, 1, scale=scale, drift_tol=tol)
+    R, V = pic.pic_get_particles(h)
+    E, edges = OL.mesh_field(c, R0)
+    plain = oracle.etd_step(c, R0, V0)
+    dR = np.full(R0.size, scale[0] * 1.0)
+    dV = np.full(R0.size, scale[1] * -0.75)
+    Ro, Vo, keep, margin = OL.learned_apply(c, plain.R, plain.V, dR, dV, tol, E, edges)
+    sure_keep, sure_fb = _oracle_certainty(c, plain, dR, dR, dV, dV, tol, E, edges)
+    sure = sure_keep | sure_fb
+    assert sure.mean() > 0.999 and 0.05 < keep.mean() < 0.95, (sure.mean(), keep.mean())
+    assert bit_equal(R[sure], Ro[sure]) and bit_equal(V[sure], Vo[sure])
+    assert int(sure_fb.sum()) <= n_fb <= int(sure_fb.sum() + (~sure).sum())
+    # the off-mesh particles are among those decided
+    off = np.abs(R0) > 2.0
+    assert off.sum() > 100 and sure[off].all()
+    pic.pic_destroy(h)
+    m.close()
+
+
+def test_learned_step_network_matches_oracle_on_poisson():
+    # a non-trivial network (random weights, nonzero biases): the oracle gives
+    # an interval for each binary32 network output (oracle.mlp's interval
+    # form); the decision is compared wherever it is the same over the whole
+    # interval, and a kept state must lie in the corrected interval
+    p = pic.pic_default_params(dt=0.4, r_min=-2.0, r_max=2.0)
+    c = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(20_001, seed=22)
+    w = inputs.mlp_init(23)
+    rng = np.random.default_rng(24)
+    pp = omlp.unflatten(w.astype(np.float64))
+    for b in ("b1", "b2", "b3"):
+        pp[b] = rng.normal(0, 0.1, pp[b].shape)
+    w = omlp.flatten(pp).astype(np.float32)
+    scale, tol = (2.0 ** -8, 2.0 ** -8), 1e-3  # powers of two: the products are exact
+    m = pic.pic_mlp_create(16)
+    pic.pic_mlp_set_weights(m, w)
+    h = pic.pic_init(p, R0, V0)
+    n_fb = pic.pic_step_learned(h, m, 1, scale=scale, drift_tol=tol)
+    R, V = pic.pic_get_particles(h)
+    E, edges = OL.mesh_field(c, R0)
+    plain = oracle.etd_step(c, R0, V0)
+    X = OL.network_inputs(R0, V0, 0.0, c.eps, c.dt).astype(np.float64)
+    iv = omlp.forward_interval(w.astype(np.float64), X)["out"]
+    dR_lo, dR_hi = scale[0] * iv.lo[:, 0], scale[0] * iv.hi[:, 0]
+    dV_lo, dV_hi = scale[1] * iv.lo[:, 1], scale[1] * iv.hi[:, 1]
+    sure_keep, sure_fb = _oracle_certainty(c, plain, dR_lo, dR_hi, dV_lo, dV_hi, tol, E, edges)
+    nonzero = ~((dR_lo <= 0) & (dR_hi >= 0) & (dV_lo <= 0) & (dV_hi >= 0))
+    sure_keep &= nonzero
+    sure_fb &= nonzero
+    sure = sure_keep | sure_fb
+    assert sure.mean() > 0.95 and sure_keep.sum() > 1000 and sure_fb.sum() > 1000, (sure.mean(), sure_keep.sum())
+    # fallbacks: the plain state bit for bit
+    assert bit_equal(R[sure_fb], plain.R[sure_fb]) and bit_equal(V[sure_fb], plain.V[sure_fb])
+    # kept: inside the interval of the corrected state (an FP64 sum rounds to nearest)
+    lo_R = np.nextafter(plain.R + dR_lo, -np.inf)
+    hi_R = np.nextafter(plain.R + dR_hi, np.inf)
+    lo_V = np.nextafter(plain.V + dV_lo, -np.inf)
+    hi_V = np.nextafter(plain.V + dV_hi, np.inf)
+    k = sure_keep
+    assert np.all((R[k] >= lo_R[k]) & (R[k] <= hi_R[k])) and np.all((V[k] >= lo_V[k]) & (V[k] <= hi_V[k]))
+    assert not np.any((R[k] == plain.R[k]) & (V[k] == plain.V[k]))
+    assert int(sure_fb.sum()) <= n_fb <= int(sure_fb.sum() + (~sure).sum())
+    pic.pic_destroy(h)
+    m.close()
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def test_adam_step_matches_oracle():
+    # two Adam steps with given gradients (one of them zero or tiny in places)
+    # against Kingma & Ba's update in FP64 with the same binary32 hyper-parameters:
+    # within 2 binary32 ulps of the weight plus 32 u of the updates
+    n = omlp.N_PARAMS
+    rng = np.random.default_rng(31)
+    w0 = (rng.normal(0, 0.3, n)).astype(np.float32)
+    g1 = rng.normal(0, 1e-2, n).astype(np.float32)
+    g2 = rng.normal(0, 1e-2, n).astype(np.float32)
+    g1[:50] = 0.0
+    g2[50:100] = 1e-10
+    lr, b1, b2, e = _f32(1e-3), _f32(0.9), _f32(0.999), _f32(1e-8)
+    m = pic.pic_mlp_create(16)
+    pic.pic_mlp_set_weights(m, w0)
+    pic.pic_mlp_apply_gradient(m, g1, lr=lr, beta1=b1, beta2=b2, eps=e)
+    w1 = pic.pic_mlp_get_weights(m)
+    pic.pic_mlp_apply_gradient(m, g2, lr=lr, beta1=b1, beta2=b2, eps=e)
+    w2 = pic.pic_mlp_get_weights(m)
+    m.close()
+    o1, mo, vo = OL.adam_step(w0.astype(np.float64), np.zeros(n), np.zeros(n), g1, 1, lr, b1, b2, e)
+    o2, _, _ = OL.adam_step(o1, mo, vo, g2, 2, lr, b1, b2, e)
+    u = 2.0 ** -24
+    ulp = np.spacing(np.abs(w0).astype(np.float32)).astype(np.float64)
+    up1, up2 = np.abs(o1 - w0), np.abs(o2 - o1)
+    assert np.all(np.abs(w1 - o1) <= ulp + 32 * u * up1)
+    assert np.all(np.abs(w2 - o2) <= 2 * ulp + 32 * u * (up1 + up2))
+    assert np.array_equal(w1[:50], w0[:50])  # a zero first gradient leaves the weight
+
+
+def _library_n_seq(B):
+    """Longest chain of sequential additions in the library's batch sums: a
+    block sums a chunk of samples (a multiple of 64, at most 256 blocks),
+    then the block partials are added in block order."""
+    nwg = min(-(-B // 64), 256)
+    chunk = -(-(-(-B // nwg)) // 64) * 64
+    nwg = -(-B // chunk)
+    return chunk + nwg + 2
+
+
+def test_training_step_matches_oracle():
+    # one pic_mlp_train step on the whole data set against Adam applied to the
+    # oracle's gradient interval: with t = 1 the update is lr g / (|g| + eps),
+    # increasing in g, so the weights lie between the updates of the interval's ends
+    n = 2048
+    rng = np.random.default_rng(32)
+    X = np.stack([rng.normal(0, 1.5, n), rng.normal(0, 1.5, n), np.sin(rng.uniform(0, 6.3, n)),
+                  np.cos(rng.uniform(0, 6.3, n)), np.full(n, 0.4)], axis=1).astype(np.float32)
+    T = np.stack([0.3 * np.sin(X[:, 0]) * X[:, 1], 0.2 * np.cos(X[:, 1])], axis=1).astype(np.float32)
+    w0 = inputs.mlp_init(33)
+    lr, e = _f32(1e-3), _f32(1e-8)
+    m = pic.pic_mlp_create(n)
+    pic.pic_mlp_set_weights(m, w0)
+    pic.pic_mlp_train(m, _dev(X), _dev(T), batch=n, steps=1, lr=lr, eps=e, seed=0)
+    w1 = pic.pic_mlp_get_weights(m).astype(np.float64)
+    m.close()
+    _, g = omlp.grads_interval(w0.astype(np.float64), X.astype(np.float64), T.astype(np.float64), _library_n_seq(n))
+    f = lambda x: x / (np.abs(x) + e)  # noqa: E731
+    w = w0.astype(np.float64)
+    ulp = np.spacing(np.abs(w0)).astype(np.float64)
+    slack = ulp + 32 * 2.0 ** -24 * lr
+    assert np.all(w1 >= w - lr * f(g.hi) - slack) and np.all(w1 <= w - lr * f(g.lo) + slack)

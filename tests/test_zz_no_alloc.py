@@ -65,3 +65,49 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     assert rc == pic.PIC_ERR_TOO_LARGE
     assert np.all(np.isnan(E))  # nothing ran
     assert "fixed scratch capacity" in pic.pic_strerror(rc)
+
+
+def _pool_bytes():
+    """(used, reserved) bytes of the current device's default memory pool
+    (the pool cudaMallocAsync draws on), read through the driver API."""
+    import ctypes
+
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev, pool = ctypes.c_int(), ctypes.c_void_p()
+    assert cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    out = []
+    for attr in (7, 5):  # CU_MEMPOOL_ATTR_USED_MEM_CURRENT, CU_MEMPOOL_ATTR_RESERVED_MEM_CURRENT
+        v = ctypes.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+        out.append(v.value)
+    return tuple(out)
+
+
+def test_noalloc_calls_allocate_no_device_memory():
+    # after the first call on the device (which only looks up the fixed
+    # array's address), further calls leave the device's free memory, the
+    # default pool and torch's allocator exactly as they were
+    rng = np.random.default_rng(5)
+    p = pic.pic_default_params(n_cells=1024)
+    Qd = torch.from_numpy(rng.integers(0, 1 << 40, p.n_cells + 1).astype(np.int64)).cuda()
+    E = torch.empty(p.n_cells + 1, dtype=torch.float64, device="cuda")
+    edges = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert pic.pic_poisson_noalloc(p, 10**6, Qd, E, edges) == pic.PIC_OK
+    torch.cuda.synchronize()
+    before = (torch.cuda.mem_get_info()[0], _pool_bytes(), torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+    for _ in range(3):
+        assert pic.pic_poisson_noalloc(p, 10**6, Qd, E, edges) == pic.PIC_OK
+    torch.cuda.synchronize()
+    after = (torch.cuda.mem_get_info()[0], _pool_bytes(), torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+    assert before == after
+
+
+def test_noalloc_rejects_a_degenerate_mesh_as_a_bad_argument():
+    for n_cells in (0, -4):
+        p = pic.pic_default_params()
+        p.n_cells = n_cells
+        rc = pic.pic_poisson_noalloc(p, 1000, torch.zeros(4, dtype=torch.int64, device="cuda"),
+                                     torch.zeros(4, dtype=torch.float64, device="cuda"),
+                                     torch.zeros(2, dtype=torch.float64, device="cuda"))
+        assert rc == pic.PIC_ERR_INVALID_ARG
