@@ -1,9 +1,11 @@
 """The batched form: many FP32 beams in one cooperative launch.
 
 Every beam of a batch must compute, bit for bit, what pic_step computes for
-it alone (the FP32 form, itself checked against the FP64 oracle in
-tests/test_gpu_f32.py), whatever the launch shape, the block share of each
-beam, the sort period and whether the step runs from a captured graph.
+it alone, whatever the launch shape, the block share of each beam, the sort
+period and whether the step runs from a captured graph; and every beam of a
+mixed batch (eps 0.1 and 0.001, 128 and 2048 cells, Poisson, Duffing with
+periods once and zero field, particles off the mesh) must match the FP64
+oracle's macro steps within the binary32 bound of the FP32 form.
 """
 import numpy as np
 import pytest
@@ -115,3 +117,61 @@ def test_batch_rejects_the_fp64_path():
     with pytest.raises(pic.PicError) as ei:
         pic.pic_batch_create([pic.pic_default_params(precision=0)], [(R0, V0)])
     assert ei.value.status == pic.PIC_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- against the FP64 oracle
+
+import oracle  # noqa: E402
+from tests.gpu_common import cfg_of  # noqa: E402
+from tests.test_gpu_f32 import etd_bound, f32, max_err  # noqa: E402
+
+# eps 0.1 and 0.001 x meshes of 128 and 2048 cells (Poisson), the Duffing
+# field with periods once and the zero field at both eps, and a beam whose
+# Gaussian tail reaches beyond a mesh on [-2, 2]
+ORACLE_SPECS = (
+    [dict(eps=e, n_cells=c, n=3001 + i) for i, (e, c) in enumerate([(0.1, 128), (0.1, 2048), (0.001, 128),
+                                                                    (0.001, 2048)])]
+    + [dict(eps=e, field_model=pic.PIC_FIELD_DUFFING, periods_once=1, n=2500) for e in (0.1, 0.001)]
+    + [dict(eps=e, field_model=pic.PIC_FIELD_ZERO, n=1500) for e in (0.1, 0.001)]
+    + [dict(eps=0.01, n_cells=256, r_min=-2.0, r_max=2.0, n=4000, uncut=True)]
+)
+
+
+def test_every_beam_of_a_mixed_batch_matches_the_oracle():
+    # each beam of one batched launch against the FP64 oracle's macro steps
+    # from the same binary32 initial state, within the binary32 bound of the
+    # FP32 form (tests/test_gpu_f32.py); charge conserved exactly
+    n_macro = 2
+    params, beams = [], []
+    for i, sp in enumerate(ORACLE_SPECS):
+        kw = {k: v for k, v in sp.items() if k not in ("n", "uncut")}
+        params.append(pic.pic_default_params(precision=1, dt=0.1, **kw))
+        poisson = sp.get("field_model", 0) == pic.PIC_FIELD_POISSON
+        R0, V0 = inputs.gaussian_beam(sp["n"], seed=60 + i, r_cut=4.0 if poisson and not sp.get("uncut") else None)
+        beams.append((f32(R0).astype(np.float64), f32(V0).astype(np.float64)))
+    b = pic.pic_batch_create(params, beams)
+    pic.pic_batch_step(b, n_macro)
+    off_mesh = 0
+    for i, (sp, p, (R0, V0)) in enumerate(zip(ORACLE_SPECS, params, beams)):
+        R, V = pic.pic_batch_get_particles(b, i)
+        m = pic.pic_batch_moments(b, i)
+        cfg = cfg_of(p)
+        T = oracle.periods(cfg, R0, V0)[0] if p.periods_once else None
+        Ro, Vo, K, N_max = R0, V0, 0, 0
+        for _ in range(n_macro):
+            res = oracle.etd_step(cfg, Ro, Vo, T)
+            Ro, Vo = res.R, res.V
+            K = max(K, res.stats["window_steps"])
+            N_max = max(N_max, int(res.N.max()))
+        scale = max(1.0, float(np.max(np.hypot(Ro, Vo))))
+        bound = etd_bound(n_macro, K, N_max, scale)
+        er, ev = max_err(R, Ro), max_err(V, Vo)
+        print(f"beam {i} {sp}: max err R {er:.3e} V {ev:.3e} (bound {bound:.3e}), K {K}, N max {N_max}")
+        assert er <= bound and ev <= bound, (i, sp, er, ev, bound)
+        if p.field_model == pic.PIC_FIELD_POISSON:
+            assert m["Q_total"] + m["n_out_of_mesh"] * p.weight_fixed == sp["n"] * p.weight_fixed
+            if sp.get("uncut"):
+                off_mesh = m["n_out_of_mesh"]
+        assert m["n_steps"] == n_macro
+    assert off_mesh > 0
+    b.close()
