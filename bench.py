@@ -9,12 +9,20 @@ for every particle (period detection, fine window with a full field cycle
 per stage, landing, extrapolation).  Metric: particle-steps/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload vp1e6|duffing1e4|vp1e8_f32]
+                    [--workload vp1e6|duffing1e4|vp1e8_f32|...] [--no-forms]
 
 `vp1e8_f32` is the FP32 form (precision 1): eps = 0.001, N_p = 1e8, 1024
 cells on [-4, 4], dt = 0.1; its line also carries the error of the FP32
 form against the FP64 path (itself bit-identical to the FP64 oracle) on a
 1e6-particle run of the same physics.
+
+With the default workload at N = 1 the line also carries `forms`: the other
+forms measured in the same run, each with its own timing, roofline and
+clocks -- the FP32 form on the same physics as the FP64 headline (with its
+error against the FP64 path), the learned stepper (with its errors against
+the fine-solver reference) beside the plain FP64 and FP32 steps of its own
+physics, the batched form, and 150 steps of the headline step for a longer
+clock record (`--no-forms` skips them).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 (the only reference this method has) on a bounded sample of the same
@@ -70,6 +78,17 @@ WORKLOADS = {
                          "{0.1, 0.05, 0.01, 0.005, 0.001}, N_r in {128, 256, 512, 1024} on [-4, 4], Poisson (3/4) and "
                          "Duffing (periods once) fields, dt = 0.1, FP32 form, one cooperative graph-replayed launch "
                          "per macro step, autotuned launch shape"),
+    # the FP32 form on the physics of vp1e6 (the same-physics comparison with the FP64 headline)
+    "vp1e6_f32": dict(n=10**6, params=dict(precision=1, sort_every=4), r_cut=4.0, error_n=10**6, error_steps=20,
+                      desc="Vlasov-Poisson FP32 form, eps=0.01, N_p=1e6, N_r=256 on [-4,4], CIC, dt=0.1, Lawson RK4 "
+                           "in the rotating frame, binary32 state, FP64 field conversion and diagnostics"),
+    # the plain steps on the learned stepper's physics (dt = 0.4, 1e7 particles, 512 cells)
+    "learned1e7_plain64": dict(n=10**7, params=dict(precision=0, dt=0.4, n_cells=512, sort_every=4), r_cut=4.0,
+                               desc="Plain improved-ETD step (FP64) on the learned stepper's physics: Vlasov-Poisson, "
+                                    "eps=0.01, N_p=1e7, N_r=512 on [-4,4], dt=0.4"),
+    "learned1e7_plain32": dict(n=10**7, params=dict(precision=1, dt=0.4, n_cells=512, sort_every=4), r_cut=4.0,
+                               desc="Plain improved-ETD step (FP32 form) on the learned stepper's physics: "
+                                    "Vlasov-Poisson, eps=0.01, N_p=1e7, N_r=512 on [-4,4], dt=0.4"),
     # FP32 form of the same physics at eps = 1e-3 (N about 15 periods per step)
     "vp1e8_f32": dict(n=10**8, params=dict(precision=1, eps=1e-3, n_cells=1024, max_window_steps=202, sort_every=4),
                       r_cut=4.0, error_n=10**6, error_steps=20,
@@ -143,7 +162,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -187,30 +206,96 @@ def make_params(pic, wl):
     return pic.pic_default_params(**WORKLOADS[wl]["params"])
 
 
-def run_ours(args):
+def time_steps(pic, h, do_step, steps, warmup, stream, rank_sync=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    handle's stream with an L2 flush (256 MB write) between them, under the
+    clock sampler.  Returns (per-step ms, window ms per step, kernel launches,
+    wall s, clocks, window launches of the last step)."""
     import torch
-    import torch.distributed as dist
 
-    from paper_1404_1160_gb300 import build as _build
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(warmup):
+        do_step()
+    torch.cuda.synchronize()
+    if rank_sync:
+        rank_sync()
+    launches0 = pic.pic_launch_count(h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    win_ms, win_n = [], []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
+            evs[k][0].record(stream)
+            do_step()
+            evs[k][1].record(stream)
+            wt = pic.pic_window_time(h)  # window kernel(s), timed by the library on this stream
+            win_ms.append(wt[0])
+            win_n.append(int(wt[1]))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    return step_ms, win_ms, pic.pic_launch_count(h) - launches0, wall, clk.summary(), (win_n[-1] if win_n else 0)
+
+
+def roofline_of(prm, wl_name, n, K, kern_ms, scheme=None, timed_K=None, win_n=0):
+    """Roofline object of the dominant kernel: the FP32 window against the
+    measured HBM copy bandwidth (streamed bytes), the FP64 window against the
+    derived FP64 peak (flops)."""
+    if not kern_ms:
+        return None
+    if prm.field_model != 0:
+        return None
+    if prm.precision == 1:
+        bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * n * K
+        achieved = bytes_ / (kern_ms / 1e3)
+        peak = measured_hbm_peak()
+        return {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": kernel_traffic(n, wl_name),
+                "kernel": "k_window32_coop (FP32 form, one launch per macro step)",
+                "kernel_ms": kern_ms, "fine_steps_per_launch": K, "algorithmic_bytes_per_launch": bytes_,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth), of measured"}
+    if scheme is not None:
+        # the comparator's step runs several windows (the fine solves over P
+        # and o, and for the modified scheme the period detection); its
+        # window time is their sum, its fine steps theirs
+        K = float(np.mean(timed_K))
+        flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
+        achieved = flops / (kern_ms / 1e3)
+        return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
+                "kernel": "k_window_coop (Lawson RK4 fine solves of the comparator step)",
+                "kernel_ms": kern_ms, "fine_steps_per_step": K, "window_launches_per_step": win_n,
+                "flops_per_step": flops,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)"}
+    flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
+    achieved = flops / (kern_ms / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_FLOPS, "traffic": kernel_traffic(n, wl_name),
+            "kernel": "k_window_coop (Lawson RK4, one launch per macro step)",
+            "kernel_ms": kern_ms, "fine_steps_per_launch": K, "flops_per_launch": flops,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)"}
+
+
+def measure(wl_name, n, steps, warmup, rank=0, world=1, with_e2e=True, with_errors=True, rank_sync=None):
+    """Times `steps` macro steps of a workload (its line, without the
+    harness keys).  The network of a learned workload is trained first,
+    outside the timed region."""
+    import torch
+
     from paper_1404_1160_gb300 import inputs
     from paper_1404_1160_gb300 import pic
 
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    _build.build()
-    wl = WORKLOADS[args.workload]
-    n = args.n_particles or wl["n"]
+    wl = WORKLOADS[wl_name]
     # replicas: every rank advances its own beam (different seed)
     R0, V0 = inputs.gaussian_beam(n, seed=rank, r_cut=wl["r_cut"])
-    prm = make_params(pic, args.workload)
+    prm = make_params(pic, wl_name)
     stream = torch.cuda.current_stream()
     lw = wl.get("learned")
     net = None
     learned_info = None
     if lw:
-        # train the correction network before anything is timed
         from paper_1404_1160_gb300 import learned as _learned
 
         t_tr = time.perf_counter()
@@ -222,7 +307,6 @@ def run_ours(args):
                         "train_s": time.perf_counter() - t_tr}
     h = pic.pic_init(prm, torch.from_numpy(R0).cuda(), torch.from_numpy(V0).cuda(), stream)
     n_fb = [0]
-
     scheme = wl.get("scheme")
     classic_K = []  # fine steps of each timed comparator step
 
@@ -233,136 +317,161 @@ def run_ours(args):
             pic.pic_step(h, 1)
         else:
             n_fb[0] += pic.pic_step_learned(h, net, 1, scale=tuple(out_scale), drift_tol=lw["tol"])
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    for _ in range(args.warmup):
-        do_step()
-    torch.cuda.synchronize()
-    n_fb[0] = 0
-    if world > 1:
-        dist.barrier()
-    launches0 = pic.pic_launch_count(h)
-    classic_K.clear()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        win_ms, win_n = [], []
-        for k in range(args.steps):
-            flush.fill_(float(k))  # L2 flush between timed steps (outside the step events)
-            evs[k][0].record(stream)
-            do_step()
-            evs[k][1].record(stream)
-            wt = pic.pic_window_time(h)  # window kernel(s), timed by the library on this stream
-            win_ms.append(wt[0])
-            win_n.append(int(wt[1]))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    timed_K = classic_K[:args.steps]
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+
+    def reset_counts():
+        n_fb[0] = 0
+        classic_K.clear()
+        if rank_sync:
+            rank_sync()
+
+    step_ms, win_ms, launches, wall, clocks, win_n = time_steps(pic, h, do_step, steps, warmup, stream, reset_counts)
+    timed_K = classic_K[:steps]
     kernel_ms = [w for w in win_ms if w > 0.0]
-    launches = pic.pic_launch_count(h) - launches0
     dev_s = sum(step_ms) / 1e3
     if world > 1:
+        import torch.distributed as dist
+
         t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dev_s = float(t.item())
-    value = world * n * args.steps / dev_s
+    value = world * n * steps / dev_s
     mom = pic.pic_moments(h)
-
-    # end to end through the public API with host buffers: H2D of the
-    # step's input (pinned), the step, D2H of the result
-    r_h = torch.from_numpy(R0.copy()).pin_memory()
-    v_h = torch.from_numpy(V0.copy()).pin_memory()
-    r_o = torch.empty(n, dtype=torch.float64).pin_memory()
-    v_o = torch.empty(n, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    parts = []  # host time of the three calls of each step (they synchronise)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ta = time.perf_counter()
-        pic.pic_set_particles(h, r_h, v_h)
-        tb = time.perf_counter()
-        do_step()
-        tc = time.perf_counter()
-        pic.pic_get_particles(h, r_o, v_o)
-        parts.append((tb - ta, tc - tb, time.perf_counter() - tc))
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    pm = np.mean(np.array(parts), axis=0) * 1e3
-    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n,
-           "mean_ms": {"set_particles": float(pm[0]), "step": float(pm[1]), "get_particles": float(pm[2])}}
+    e2e = None
+    if with_e2e:
+        # end to end through the public API with host buffers: H2D of the
+        # step's input (pinned), the step, D2H of the result
+        r_h = torch.from_numpy(R0.copy()).pin_memory()
+        v_h = torch.from_numpy(V0.copy()).pin_memory()
+        r_o = torch.empty(n, dtype=torch.float64).pin_memory()
+        v_o = torch.empty(n, dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, min(steps, 5))
+        parts = []  # host time of the three calls of each step (they synchronise)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ta = time.perf_counter()
+            pic.pic_set_particles(h, r_h, v_h)
+            tb = time.perf_counter()
+            do_step()
+            tc = time.perf_counter()
+            pic.pic_get_particles(h, r_o, v_o)
+            parts.append((tb - ta, tc - tb, time.perf_counter() - tc))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        pm = np.mean(np.array(parts), axis=0) * 1e3
+        e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 16 * n,
+               "mean_ms": {"set_particles": float(pm[0]), "step": float(pm[1]), "get_particles": float(pm[2])}}
     pic.pic_destroy(h)
-
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    mean_ms = float(np.mean(step_ms))
+        if net is not None:
+            net.close()
+        return None
     K = mom["window_steps"]
-    roofline = None
     f32 = prm.precision == 1
-    if f32 and prm.field_model == 0 and kernel_ms:
-        kern_ms = float(np.mean(kernel_ms))
-        bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * n * K
-        achieved = bytes_ / (kern_ms / 1e3)
-        peak = measured_hbm_peak()
-        roofline = {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": kernel_traffic(n, args.workload),
-                    "kernel": "k_window32_coop (FP32 form, one launch per macro step)",
-                    "kernel_ms": kern_ms, "fine_steps_per_launch": K, "algorithmic_bytes_per_launch": bytes_,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
-    elif prm.field_model == 0 and kernel_ms and scheme is not None:
-        # the comparator's step runs several windows (the fine solves over P
-        # and o, and for the modified scheme the period detection); its
-        # window time is their sum, its fine steps theirs
-        K = float(np.mean(timed_K))
-        kern_ms = float(np.mean(kernel_ms))
-        flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
-        achieved = flops / (kern_ms / 1e3)
-        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_FLOPS, "traffic": None,
-                    "kernel": "k_window_coop (Lawson RK4 fine solves of the comparator step)",
-                    "kernel_ms": kern_ms, "fine_steps_per_step": K,
-                    "window_launches_per_step": win_n[-1],
-                    "flops_per_step": flops,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)"}
-    elif prm.field_model == 0 and kernel_ms and scheme is None:
-        kern_ms = float(np.mean(kernel_ms))
-        flops = FLOPS_PER_PARTICLE_FINE_STEP * n * K
-        achieved = flops / (kern_ms / 1e3)
-        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_FLOPS, "traffic": kernel_traffic(n, args.workload),
-                    "kernel": "k_window_coop (Lawson RK4, one launch per macro step)",
-                    "kernel_ms": kern_ms, "fine_steps_per_launch": K,
-                    "flops_per_launch": flops,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)"}
+    roofline = roofline_of(prm, wl_name, n, K, float(np.mean(kernel_ms)) if kernel_ms else None, scheme, timed_K,
+                           win_n)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if f32 else "f64",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "n_particles": n, "fine_steps_per_window": K,
+        "config": {"workload": wl["desc"], "n_particles": n, "fine_steps_per_window": K, "dt": prm.dt,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "L2 flushed between timed steps (256 MB write); per-step trajectory store > L2"},
         "roofline": roofline,
-        "e2e": e2e,
         "gpu_launches": int(launches),
         "wall_s": wall,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "error_vs_oracle": ("FP32 form: see error_vs_fp64 (binary32 bounds checked against the FP64 oracle in the "
                             "parity tests)") if f32 else
                            "bit-identical R, V and charge on the parity tests (tolerance 1e-12 rel)",
     }
-    if f32 and "error_n" in wl:
-        line["error_vs_fp64"] = error_vs_fp64(args.workload)
+    if e2e is not None:
+        line["e2e"] = e2e
+    if with_errors and f32 and "error_n" in wl:
+        line["error_vs_fp64"] = error_vs_fp64(wl_name)
     if lw:
-        learned_info["fallback_fraction"] = n_fb[0] / float(n * args.steps)
-        learned_info.update(learned_errors(prm, wl, net, out_scale))
+        learned_info["fallback_fraction"] = n_fb[0] / float(n * steps)
+        if with_errors:
+            learned_info.update(learned_errors(prm, wl, net, out_scale))
         line["learned"] = learned_info
         net.close()
+    return line
+
+
+def form_summary(line, ref_value=None, ref_dt=None):
+    """The keys of a form entry: its throughput, timing, roofline, clocks and
+    errors; with the FP64 headline's value, the speed-up per macro step and
+    per unit of simulated time."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "clocks",
+            "gpu_launches", "error_vs_fp64", "learned", "error_vs_oracle")
+    out = {k: line[k] for k in keep if k in line}
+    if ref_value:
+        out["vs_fp64_headline"] = line["value"] / ref_value
+        dt = line["config"].get("dt")
+        if dt and ref_dt:
+            out["vs_fp64_headline_per_simulated_time"] = line["value"] * dt / (ref_value * ref_dt)
+    return out
+
+
+def measure_forms(head_line, head_dt):
+    """The other forms, measured in the same run as the FP64 headline: the FP32
+    form on the same physics, the learned stepper with the plain FP64 and FP32
+    steps of its own physics beside it, the batched form, and a longer run of
+    the headline step for its clock record.  A form that fails records its error."""
+    forms = {}
+    ref = head_line["value"]
+    plan = [
+        ("fp32_same_physics", lambda: form_summary(measure("vp1e6_f32", WORKLOADS["vp1e6_f32"]["n"], 30, 3,
+                                                           with_e2e=False), ref, head_dt)),
+        ("learned", lambda: form_summary(measure("learned1e7", WORKLOADS["learned1e7"]["n"], 10, 3,
+                                                 with_e2e=False), ref, head_dt)),
+        ("plain_fp64_learned_physics", lambda: form_summary(measure("learned1e7_plain64",
+                                                                    WORKLOADS["learned1e7_plain64"]["n"], 5, 3,
+                                                                    with_e2e=False, with_errors=False),
+                                                            ref, head_dt)),
+        ("plain_fp32_learned_physics", lambda: form_summary(measure("learned1e7_plain32",
+                                                                    WORKLOADS["learned1e7_plain32"]["n"], 10, 3,
+                                                                    with_e2e=False, with_errors=False),
+                                                            ref, head_dt)),
+        ("batch64", lambda: form_summary(measure_batch("batch64", 10, 3, with_e2e=False)[0], ref, head_dt)),
+        ("fp64_sustained", lambda: form_summary(measure("vp1e6", WORKLOADS["vp1e6"]["n"], 150, 3, with_e2e=False,
+                                                        with_errors=False), ref, head_dt)),
+    ]
+    for name, fn in plan:
+        t0 = time.perf_counter()
+        try:
+            forms[name] = fn()
+        except Exception as e:  # a failing form must not lose the headline line
+            forms[name] = {"error": f"{type(e).__name__}: {e}"}
+        forms[name]["run_s"] = time.perf_counter() - t0
+    return forms
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1404_1160_gb300 import build as _build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    wl = WORKLOADS[args.workload]
+    n = args.n_particles or wl["n"]
+    line = measure(args.workload, n, args.steps, args.warmup, rank, world,
+                   rank_sync=(lambda: dist.barrier()) if world > 1 else None)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
+    if args.workload == "vp1e6" and world == 1 and not args.no_forms and not args.n_particles:
+        line["forms"] = measure_forms(line, WORKLOADS["vp1e6"]["params"].get("dt", 0.1))
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -392,16 +501,14 @@ def batch_specs(wl):
     return params, beams
 
 
-def run_batch(args):
+def measure_batch(wl_name, steps, warmup, with_e2e=True):
+    """Times `steps` batched macro steps (after autotuning, whose trial steps
+    are real steps); returns the line without the harness keys."""
     import torch
 
-    from paper_1404_1160_gb300 import build as _build
     from paper_1404_1160_gb300 import pic
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    _build.build()
-    wl = WORKLOADS[args.workload]
+    wl = WORKLOADS[wl_name]
     params, beams = batch_specs(wl)
     sizes = np.array([r.size for r, _ in beams])
     n_total = int(sizes.sum())
@@ -410,15 +517,15 @@ def run_batch(args):
     t_tune = time.perf_counter()
     tuned = pic.pic_batch_tune(b, steps_per_trial=2)  # real steps; they also warm up
     t_tune = time.perf_counter() - t_tune
-    pic.pic_batch_step(b, args.warmup)
+    pic.pic_batch_step(b, warmup)
     torch.cuda.synchronize()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     launches0 = pic.pic_batch_launch_count(b)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
             pic.pic_batch_step(b, 1)
@@ -427,50 +534,66 @@ def run_batch(args):
         wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(c) for a, c in evs]
     dev_s = sum(step_ms) / 1e3
-    value = n_total * args.steps / dev_s
+    value = n_total * steps / dev_s
     launches = pic.pic_batch_launch_count(b) - launches0
     Ks = np.array([pic.pic_batch_moments(b, i)["window_steps"] for i in range(len(beams))])
-    # end to end with host buffers: every beam's (R, V) in and out each step
-    host = [(torch.from_numpy(r.copy()).pin_memory(), torch.from_numpy(v.copy()).pin_memory()) for r, v in beams]
-    outs = [(torch.empty(r.size, dtype=torch.float64).pin_memory(), torch.empty(r.size, dtype=torch.float64).pin_memory())
-            for r, _ in beams]
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for i, (r, v) in enumerate(host):
-            pic.pic_batch_set_particles(b, i, r, v)
-        pic.pic_batch_step(b, 1)
-        for i, (r, v) in enumerate(outs):
-            pic.pic_batch_get_particles_into(b, i, r, v)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e = None
+    if with_e2e:
+        # end to end with host buffers: every beam's (R, V) in and out each step
+        host = [(torch.from_numpy(r.copy()).pin_memory(), torch.from_numpy(v.copy()).pin_memory()) for r, v in beams]
+        outs = [(torch.empty(r.size, dtype=torch.float64).pin_memory(),
+                 torch.empty(r.size, dtype=torch.float64).pin_memory()) for r, _ in beams]
+        e2e_steps = max(1, min(steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for i, (r, v) in enumerate(host):
+                pic.pic_batch_set_particles(b, i, r, v)
+            pic.pic_batch_step(b, 1)
+            for i, (r, v) in enumerate(outs):
+                pic.pic_batch_get_particles_into(b, i, r, v)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": n_total * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n_total,
+               "d2h_bytes_per_step": 16 * n_total}
     b.close()
-    if rank != 0:
-        return
     mean_ms = float(np.mean(step_ms))
     bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * float(np.sum(sizes * Ks))
     peak = measured_hbm_peak()
     achieved = bytes_ / (mean_ms / 1e3)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
         "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "n_beams": len(beams), "n_particles_total": n_total,
-                   "n_particles_min": int(sizes.min()), "n_particles_max": int(sizes.max()),
+                   "n_particles_min": int(sizes.min()), "n_particles_max": int(sizes.max()), "dt": wl["batch"]["dt"],
                    "fine_steps_per_window_max": int(Ks.max()), "tuned": tuned, "tune_s": t_tune,
                    "parallelism": "single GPU", "l2": "L2 flushed between timed steps (256 MB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_window32_batch (all beams, one cooperative launch per macro step)",
                      "kernel_ms": mean_ms, "algorithmic_bytes_per_launch": bytes_,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"},
-        "e2e": {"value": n_total * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * n_total,
-                "d2h_bytes_per_step": 16 * n_total},
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth), of measured"},
         "gpu_launches": int(launches), "wall_s": wall, "clocks": clk.summary(),
-        "error_vs_oracle": "every beam bit-identical to the FP32 form run alone (tests/test_gpu_batch.py), which is "
-                           "checked against the FP64 oracle within binary32 bounds (tests/test_gpu_f32.py)",
+        "error_vs_oracle": "every beam bit-identical to the FP32 form run alone, and every beam of a mixed batch "
+                           "within the binary32 bound of the FP64 oracle (tests/test_gpu_batch.py)",
     }
+    if e2e is not None:
+        line["e2e"] = e2e
+    return line, params, beams
+
+
+def run_batch(args):
+    import torch
+
+    from paper_1404_1160_gb300 import build as _build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    line, params, beams = measure_batch(args.workload, args.steps, args.warmup)
+    if rank != 0:
+        return
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline(params, beams)
     print(json.dumps(line))
@@ -728,6 +851,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--n-particles", type=int, default=0, help="override N_p (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="default workload: skip the other forms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
