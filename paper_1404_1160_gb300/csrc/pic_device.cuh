@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "locate_fixed.cuh"
+
 namespace pic {
 
 constexpr int kMaxCellsWindow = 2048;  // mesh cells served by the fused window kernel (shared memory)
@@ -37,6 +39,7 @@ struct DevParams {
     int log2W;
     int n_cells, c;
     int xs_fma;                        // 1 when inv_hr is a power of two
+    LocFixed loc;                      // the same locate on the integer pipe (xs_fma meshes)
     // algorithm
     int field, solver;                 // PIC_FIELD_*, PIC_FINE_*
     int Kmax;                          // window cap (fine steps)
@@ -113,6 +116,9 @@ __device__ __forceinline__ void split_fixed(double xs, int log2W, long long& xi,
 template <int POW2>
 __device__ __forceinline__ Cell mesh_locate(const DevParams& P, double R) {
     Cell c;
+    // FP64 is the scarce pipe on this GPU: where the fixed-point form answers
+    // (it rounds xs exactly as the fma below does), no FP64 instruction runs
+    if (POW2 && P.loc.ok && loc_fixed(P.loc, R, c.j, c.qR, c.a)) return c;
     const double xs = mesh_xs<POW2>(P, R);
     const unsigned long long b = (unsigned long long)__double_as_longlong(xs);
     const unsigned long long mag = b & 0x7fffffffffffffffull;
