@@ -462,7 +462,7 @@ def run_ours(args):
     _build.build()
     wl = WORKLOADS[args.workload]
     n = args.n_particles or wl["n"]
-    line = measure(args.workload, n, args.steps, args.warmup, rank, world,
+    line = measure(args.workload, n, args.steps, args.warmup, rank, world, with_errors=not args.no_errors,
                    rank_sync=(lambda: dist.barrier()) if world > 1 else None)
     if rank != 0:
         if world > 1:
@@ -852,6 +852,7 @@ def main():
     ap.add_argument("--n-particles", type=int, default=0, help="override N_p (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="default workload: skip the other forms")
+    ap.add_argument("--no-errors", action="store_true", help="skip the error runs of the FP32 and learned forms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -108,6 +108,7 @@ void make_devparams(const pic_params* p, long long n, DevParams* d) {
     d->xs_max = (double)p->n_cells * d->Wd;
     d->xs_max_i = (long long)p->n_cells * (long long)p->weight_fixed;
     pic::loc_fixed_setup(&d->loc, d->xs_fma, d->xs_scale, d->xs_off, d->xs_max_i, d->log2W);
+    d->imul = 1;
     d->q_unit = n > 0 ? p->total_charge / ((double)n * d->Wd) : 0.0;
     d->q_half = 0.5 * d->q_unit;
     d->field = p->field_model;

@@ -29,14 +29,7 @@
 // tests/test_locate_fixed.py).
 #pragma once
 
-#include <stdint.h>
-#include <string.h>
-
-#if defined(__CUDACC__)
-#define PIC_HD __host__ __device__ __forceinline__
-#else
-#define PIC_HD inline
-#endif
+#include "intfp.cuh"
 
 namespace pic {
 
@@ -49,35 +42,6 @@ struct LocFixed {
     long long xs_max;  // n_cells W
     long long Wmask;   // W - 1
 };
-
-PIC_HD uint64_t lf_bits(double x) {
-#if defined(__CUDA_ARCH__)
-    return (uint64_t)__double_as_longlong(x);
-#else
-    uint64_t b;
-    memcpy(&b, &x, 8);
-    return b;
-#endif
-}
-
-PIC_HD double lf_double(uint64_t b) {
-#if defined(__CUDA_ARCH__)
-    return __longlong_as_double((long long)b);
-#else
-    double x;
-    memcpy(&x, &b, 8);
-    return x;
-#endif
-}
-
-// position of the leading one bit (x > 0)
-PIC_HD int lf_msb(uint64_t x) {
-#if defined(__CUDA_ARCH__)
-    return 63 - __clzll((long long)x);
-#else
-    return 63 - __builtin_clzll(x);
-#endif
-}
 
 // Fills L for a mesh with xs_scale = s, xs_off = C, n_cells W = xs_max,
 // W = 2^log2W (host side).

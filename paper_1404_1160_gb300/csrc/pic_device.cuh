@@ -40,6 +40,7 @@ struct DevParams {
     int n_cells, c;
     int xs_fma;                        // 1 when inv_hr is a power of two
     LocFixed loc;                      // the same locate on the integer pipe (xs_fma meshes)
+    int imul;                          // 1: products by the rotation constants on the integer pipe
     // algorithm
     int field, solver;                 // PIC_FIELD_*, PIC_FINE_*
     int Kmax;                          // window cap (fine steps)
@@ -149,6 +150,14 @@ __device__ __forceinline__ Cell mesh_locate(const DevParams& P, double R) {
     c.j = (int)(xi >> P.log2W);
     c.a = a;              // W f
     return c;
+}
+
+// x * y with the bits of the FP64 product: on the integer pipe when `on`
+// and imul64 answers (normal operands and result), else the FP64 multiply.
+__device__ __forceinline__ double dmul_i(int on, double x, double y) {
+    double r;
+    if (on && imul64(x, y, r)) return r;
+    return x * y;
 }
 
 // Exact-rounding int64 -> double (round to nearest, ties to even) with

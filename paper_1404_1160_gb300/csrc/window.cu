@@ -372,9 +372,9 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 if (SOLVER == 1) {
                     // ce = (e1, e3), ea = e2, eb = e4, cx.x = (Phi_h y)_R
                     const double e1 = in.ce.x, e3 = in.ce.y;
-                    const double Bv = fma(P.c1, V, -(P.s1 * R));
+                    const double Bv = fma(P.c1, V, -dmul_i(P.imul, P.s1, R));
                     const double e23 = ea + e3;
-                    Rn = fma(P.h6, fma(P.tsh, e23, P.s1 * e1), in.cx.x);
+                    Rn = fma(P.h6, fma(P.tsh, e23, dmul_i(P.imul, P.s1, e1)), in.cx.x);
                     Vn = fma(P.h6, fma(P.tch, e23, fma(P.c1, e1, eb)), Bv);
                 } else {
                     // ce = partial sums, cx = (R3, R4), ea = e3, eb = e4
@@ -408,8 +408,8 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             double2 cx;
             if (SOLVER == 1) {
                 ca = mesh_locate<POW2>(P, R);                            // stage 1: y
-                cb = mesh_locate<POW2>(P, fma(P.sh, V, P.ch * R));       // stage 3: Phi_h/2 y
-                cx = make_double2(fma(P.s1, V, P.c1 * R), 0.0);          // (Phi_h y)_R
+                cb = mesh_locate<POW2>(P, fma(P.sh, V, dmul_i(P.imul, P.ch, R)));  // stage 3: Phi_h/2 y
+                cx = make_double2(fma(P.s1, V, dmul_i(P.imul, P.c1, R)), 0.0);  // (Phi_h y)_R
             } else {
                 ca = mesh_locate<POW2>(P, R);                            // stage 1: y
                 const double R2 = fma(P.h2, ie * V, R);                  // stage 2: y + h/2 k1
