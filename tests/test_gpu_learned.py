@@ -418,3 +418,61 @@ def test_training_step_matches_oracle():
     ulp = np.spacing(np.abs(w0)).astype(np.float64)
     slack = ulp + 32 * 2.0 ** -24 * lr
     assert np.all(w1 >= w - lr * f(g.hi) - slack) and np.all(w1 <= w - lr * f(g.lo) + slack)
+
+
+@pytest.mark.parametrize("field", [pic.PIC_FIELD_DUFFING, pic.PIC_FIELD_POISSON])
+def test_specified_targets_teach_the_small_steps_error(field):
+    # The network trained on the specified targets (8 plain improved-ETD steps
+    # of dt/8 minus one step of dt) next to the same network trained on the
+    # paper's reference solution (the fine solver over dt), on the physics of
+    # the Duffing run (E = -r^3, eps = 0.01, r, v ~ N(0, 1), periods once) and
+    # of the Vlasov-Poisson run (eps = 0.01, 256 cells on [-4, 4], the cut
+    # Gaussian beam), both with dt = 0.4; errors after one step of a held-out
+    # beam against the oracle's brute-force fine solve.  For this method the
+    # large step is more accurate than 8 steps of dt/8 (its error does not grow
+    # with dt where periods are clean), so the specified targets carry mostly
+    # the small steps' own error: the network trained on them moves the large
+    # step toward the small steps, away from the reference, while the network
+    # trained on the reference solution reduces the large step's error
+    # (measured, median: Duffing plain 3.3e-5, 8 x dt/8 1.4e-4, "etd" 1.3e-4, "fine" 2.9e-5;
+    # Vlasov-Poisson plain 1.6e-5, 8 x dt/8 1.3e-4, "etd" 1.3e-4, "fine" 9.3e-8).
+    duff = field == pic.PIC_FIELD_DUFFING
+    p = pic.pic_default_params(field_model=field, dt=0.4, periods_once=1 if duff else 0)
+    cut = None if duff else 4.0
+    beams = [inputs.gaussian_beam(50_000, seed=300 + s, r_cut=cut) for s in range(2)]
+    nets = {}
+    for ref in ("etd", "fine"):
+        X, T = learned.make_dataset(p, beams, n_macro=2, reference=ref)
+        m, scale, hist, kept = learned.train(X, T, steps=1500, batch=8192, seed=1)
+        nets[ref] = (m, scale)
+    R0, V0 = inputs.gaussian_beam(20_000, seed=399, r_cut=cut)
+    cfg = cfg_of(p)
+    Rf, Vf = oracle.brute_force(cfg, R0, V0, 0.4)
+
+    def run(how):
+        h = pic.pic_init(p if how != "small" else pic.pic_default_params(field_model=field, dt=0.05,
+                                                                         periods_once=1 if duff else 0), R0, V0)
+        if how == "plain":
+            pic.pic_step(h, 1)
+        elif how == "small":
+            pic.pic_step(h, 8)
+        else:
+            m, scale = nets[how]
+            pic.pic_step_learned(h, m, 1, scale=tuple(scale), drift_tol=1e-4)
+        R, V = pic.pic_get_particles(h)
+        pic.pic_destroy(h)
+        return robust(np.hypot(R - Rf, V - Vf))[0]
+
+    err = {how: run(how) for how in ("plain", "small", "etd", "fine")}
+    print(f"field {field}: median error vs the fine reference after one step of dt = 0.4: {err}")
+    assert err["small"] > 2.0 * err["plain"]           # the specified reference is the less accurate one
+    assert err["etd"] > err["plain"]                    # ... and the network trained on it follows it
+    # the reference-solution targets never degrade the large step; on the
+    # Vlasov-Poisson beam (near equilibrium) they gain about tenfold, while the
+    # Duffing step's remaining error (the landing's interpolation remainder,
+    # which oscillates quickly across (r, v)) is learnt only in part
+    assert err["fine"] <= 1.1 * err["plain"]
+    if not duff:
+        assert err["fine"] < 0.3 * err["plain"]
+    for m, _ in nets.values():
+        m.close()
