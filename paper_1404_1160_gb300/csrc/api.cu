@@ -229,6 +229,7 @@ struct pic_handle {
     // learned stepper (allocated by the first pic_step_learned)
     void* y_prev = nullptr;
     double* psi = nullptr;
+    float* psi_f = nullptr;    // binary32 field tables of the FP32 form's energy check
     unsigned long long* n_fb = nullptr;
     double t = 0.0;
     long long n_steps = 0;
@@ -712,6 +713,7 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
         if (!rc) h->y_prev = yp;
         if (!rc) rc = dalloc(h, &h->n_fb, 1);
         if (!rc && poisson) rc = dalloc(h, &h->psi, Np1);
+        if (!rc && poisson && h->prec) rc = dalloc(h, &h->psi_f, 3 * Np1);
         if (rc) return rc;
     }
     cudaError_t e = cudaMemsetAsync(h->n_fb, 0, sizeof(unsigned long long), h->st);
@@ -726,7 +728,8 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
                         : pic::launch_deposit(h->dp, (const double*)h->B.y, h->n, 2, h->Qf, h->nout_f, h->st,
                                               h->sm_count, &h->launches);
             if (e == cudaSuccess) e = pic::launch_poisson(h->dp, h->Qf, h->Ef, h->edges_f, h->S, h->st, &h->launches);
-            if (e == cudaSuccess) e = pic::launch_psi_nodes(h->Ef, h->dp.n_cells, h->dp.hr, h->psi, h->st, &h->launches);
+            if (e == cudaSuccess)
+                e = pic::launch_psi_nodes(h->Ef, h->dp.n_cells, h->dp.hr, h->psi, h->st, &h->launches, h->psi_f);
         }
         if (e != cudaSuccess) break;
         // the plain improved-ETD step, in the order just fixed
@@ -760,6 +763,7 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
             A.n_cells = h->dp.n_cells;
         }
         A.n_fallback = h->n_fb;
+        A.tab_f = h->psi_f;
         e = pic::launch_learned_apply(m, A, h->sm_count, h->st, &h->launches);
         if (e == cudaSuccess) {
             h->t += h->prm.dt;

@@ -27,6 +27,7 @@
 #include <new>
 #include <vector>
 
+#include "energy_check.cuh"
 #include "pic_internal.h"
 
 namespace pic {
@@ -456,10 +457,35 @@ __device__ __forceinline__ double frozen_energy(const LearnedArgs& A, double R, 
     return 0.5 * (R * R + V * V) - A.eps * psi_at(A, R);
 }
 
+// The FP64 rule, out of line: it runs only for the particles the binary32
+// check leaves undecided (and for every particle of FP64 handles).
+static __device__ __noinline__ bool frozen_keep_fp64(const LearnedArgs& A, double Rp, double Vp, double Rl,
+                                                     double Vl) {
+    const double H0 = frozen_energy(A, Rp, Vp);
+    const double H1 = frozen_energy(A, Rl, Vl);
+    return fabs(H1 - H0) <= A.tol * fabs(H0);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedArgs A) {
     __shared__ MlpSmem S;
-    load_weights(M, S, false);
+    extern __shared__ float s_tab[];  // the binary32 field tables (3 (n_cells + 1)), when given
+    if (A.tab_f)
+        for (int i = threadIdx.x; i < 3 * (A.n_cells + 1); i += blockDim.x) s_tab[i] = A.tab_f[i];
+    load_weights(M, S, false);  // ends with a block barrier
+    const float* tab_f = A.tab_f ? s_tab : nullptr;
+    EnergyF32 E32;
+    E32.field = A.field;
+    E32.eps = (float)A.eps;
+    E32.tol = (float)A.tol;
+    E32.n_cells = A.n_cells;
+    E32.r_min = (float)A.r_min;
+    E32.hr = (float)A.hr;
+    E32.inv_hr = (float)A.inv_hr;
+    E32.E = tab_f;
+    E32.slope = tab_f ? tab_f + (A.n_cells + 1) : nullptr;
+    E32.psi = tab_f ? tab_f + 2 * (A.n_cells + 1) : nullptr;
+    if (A.field == PIC_FIELD_POISSON && !A.tab_f) E32.field = -1;  // no tables: every particle in FP64
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
     const long long n = A.n, tiles = (n + 15) / 16;
     unsigned int fallback = 0;
@@ -496,27 +522,30 @@ __global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedA
             const long long s = tile * 16 + g + 8 * h;
             const float o0 = h ? T.out[1][0] : T.out[0][0], o1 = h ? T.out[1][1] : T.out[0][1];
             const bool ok = h ? valid[1] : valid[0];
-            const double dR = (double)(A.scale_R * o0), dV = (double)(A.scale_V * o1);
-            if (ok && (dR != 0.0 || dV != 0.0)) {
+            const float dRf = A.scale_R * o0, dVf = A.scale_V * o1;
+            if (ok && (dRf != 0.0f || dVf != 0.0f)) {
                 double Rp, Vp, Rl, Vl;
+                int dec = -1;
                 if (PREC == 0) {
                     const double2 pl = ((const double2*)A.y)[s];
                     Rp = pl.x;
                     Vp = pl.y;
-                    Rl = pl.x + dR;
-                    Vl = pl.y + dV;
+                    Rl = pl.x + (double)dRf;
+                    Vl = pl.y + (double)dVf;
                 } else {
                     const float2 pl = ((const float2*)A.y)[s];
+                    const float R1 = pl.x + dRf, V1 = pl.y + dVf;
                     Rp = pl.x;
                     Vp = pl.y;
-                    Rl = (double)(pl.x + (float)dR);
-                    Vl = (double)(pl.y + (float)dV);
+                    Rl = (double)R1;
+                    Vl = (double)V1;
+                    // binary32 where it provably gives the FP64 decision
+                    dec = energy_check_f32(E32, pl.x, pl.y, R1, V1);
                 }
                 // the plain step judges: the correction may move the frozen-field
                 // energy away from the plain step's by at most tol |H|
-                const double H0 = frozen_energy(A, Rp, Vp);
-                const double H1 = frozen_energy(A, Rl, Vl);
-                if (fabs(H1 - H0) <= A.tol * fabs(H0)) {
+                const bool keep = dec >= 0 ? dec == 1 : frozen_keep_fp64(A, Rp, Vp, Rl, Vl);
+                if (keep) {
                     if (PREC == 0) ((double2*)A.y)[s] = make_double2(Rl, Vl);
                     else ((float2*)A.y)[s] = make_float2((float)Rl, (float)Vl);
                 } else {
@@ -530,17 +559,29 @@ __global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedA
     if (lane == 0 && fallback) atomicAdd(A.n_fallback, (unsigned long long)fallback);
 }
 
-__global__ void k_psi_nodes(const double* __restrict__ E, int n_cells, double hr, double* __restrict__ psi) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    const int c = n_cells / 2;
-    psi[c] = 0.0;
-    for (int j = c + 1; j <= n_cells; ++j) psi[j] = psi[j - 1] + (0.5 * hr) * (E[j - 1] + E[j]);
-    for (int j = c - 1; j >= 0; --j) psi[j] = psi[j + 1] - (0.5 * hr) * (E[j] + E[j + 1]);
+__global__ void k_psi_nodes(const double* __restrict__ E, int n_cells, double hr, double* __restrict__ psi,
+                            float* __restrict__ tab_f) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int c = n_cells / 2;
+        psi[c] = 0.0;
+        for (int j = c + 1; j <= n_cells; ++j) psi[j] = psi[j - 1] + (0.5 * hr) * (E[j - 1] + E[j]);
+        for (int j = c - 1; j >= 0; --j) psi[j] = psi[j + 1] - (0.5 * hr) * (E[j] + E[j + 1]);
+    }
+    if (!tab_f) return;
+    __syncthreads();
+    // binary32 copies for the energy check of the FP32 form
+    const int Np1 = n_cells + 1;
+    const double inv_hr = 1.0 / hr;
+    for (int j = threadIdx.x; j < Np1; j += blockDim.x) {
+        tab_f[j] = (float)E[j];
+        tab_f[Np1 + j] = j < n_cells ? (float)((E[j + 1] - E[j]) * inv_hr) : 0.0f;
+        tab_f[2 * Np1 + j] = (float)psi[j];
+    }
 }
 
 cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* psi, cudaStream_t st,
-                             long long* launches) {
-    k_psi_nodes<<<1, 32, 0, st>>>(E, n_cells, hr, psi);
+                             long long* launches, float* tab_f) {
+    k_psi_nodes<<<1, 256, 0, st>>>(E, n_cells, hr, psi, tab_f);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -653,11 +694,17 @@ cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_
     long long g = (tiles + 3) / 4;
     // one wave: as many blocks as are resident at once (the kernel strides over the tiles)
     auto fn = A.prec == 0 ? k_learned_apply<0> : k_learned_apply<1>;
+    const size_t smem = A.tab_f ? sizeof(float) * 3 * (size_t)(A.n_cells + 1) : 0;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFbThreads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFbThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     const long long cap = (long long)sm_count * per_sm;
     const int grid = (int)(g < 1 ? 1 : (g < cap ? g : cap));
-    fn<<<grid, kFbThreads, 0, st>>>(m->D, A);
+    fn<<<grid, kFbThreads, smem, st>>>(m->D, A);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

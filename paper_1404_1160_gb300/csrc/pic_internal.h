@@ -218,12 +218,15 @@ struct LearnedArgs {
     double r_min, hr, inv_hr;
     int n_cells;
     unsigned long long* n_fallback;
+    const float* tab_f;            // Poisson, FP32 form: E_j, slope_j, psi_j in binary32 (3 (n_cells+1))
 };
 cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_count, cudaStream_t st,
                                  long long* launches);
-// psi at the nodes from E at the nodes (trapezoid of the piecewise-linear field).
+// psi at the nodes from E at the nodes (trapezoid of the piecewise-linear field);
+// with tab_f (3 (n_cells+1) floats, may be null) also the binary32 copies of
+// E_j, (E_{j+1} - E_j)/h_r and psi_j for the energy check of the FP32 form.
 cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* psi, cudaStream_t st,
-                             long long* launches);
+                             long long* launches, float* tab_f = nullptr);
 // psi at A.n positions R (the energy check's potential), written to out.
 cudaError_t launch_psi_eval(const LearnedArgs& A, const double* R, double* out, int sm_count, cudaStream_t st);
 }  // namespace pic
