@@ -1,6 +1,7 @@
 // mlp.cu -- the network of the learned stepper: a 5-64-64-2 GELU perceptron
-// with bfloat16 weights and FP32 accumulation, inference and training on the
-// tensor cores (mma.sync m16n8k16, bf16 x bf16 -> f32).  The paper has no
+// with bfloat16 weights and FP32 accumulation on the tensor cores: inference
+// (and the learned step's correction) with tcgen05.mma into tensor memory,
+// training with warp-level mma.sync m16n8k16 (bf16 x bf16 -> f32).  The paper has no
 // learned component; the network corrects one macro step of the improved ETD
 // scheme (Algorithm ETDFSSModAlgo) and is defined, with its rounding points,
 // as:
@@ -22,6 +23,7 @@
 // order before the Adam update, so training is reproducible bit for bit.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -29,6 +31,7 @@
 
 #include "energy_check.cuh"
 #include "pic_internal.h"
+#include "tc_desc.cuh"
 
 namespace pic {
 
@@ -62,6 +65,7 @@ struct MlpDev {
     float* grad_part;     // [kWgMaxBlocks][kMParams]
     float* grad;          // [kMParams]
     float* loss;          // [1]
+    int* err;             // set by a tensor-core wait that ran out of time
 };
 
 // ------------------------------------------------------------ device math
@@ -466,14 +470,111 @@ static __device__ __noinline__ bool frozen_keep_fp64(const LearnedArgs& A, doubl
     return fabs(H1 - H0) <= A.tol * fabs(H0);
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedArgs A) {
-    __shared__ MlpSmem S;
-    extern __shared__ float s_tab[];  // the binary32 field tables (3 (n_cells + 1)), when given
-    if (A.tab_f)
-        for (int i = threadIdx.x; i < 3 * (A.n_cells + 1); i += blockDim.x) s_tab[i] = A.tab_f[i];
-    load_weights(M, S, false);  // ends with a block barrier
-    const float* tab_f = A.tab_f ? s_tab : nullptr;
+// ------------------------------------------------------------ tensor-core inference (tcgen05)
+//
+// Inference of the network (pic_mlp_forward) and the learned step's
+// correction with the 64 x 64 hidden layer on the 5th-generation tensor
+// cores: a block of 128 threads owns 128 samples (one per thread), writes
+// bf16(gelu(z1)) as the A operand (128 x 64, K-major core matrices) to shared
+// memory, and one thread issues four tcgen05.mma (M = 128, N = 64, K = 16
+// each) against W2 (B operand, 64 x 64) into a 64-column f32 accumulator in
+// tensor memory and commits them to an mbarrier; each warp then reads its 32
+// rows back with tcgen05.ld.  The output layer adds the products of each
+// sample's 64 columns in four partial sums of 16 (columns 8 nt + 2 q + e for
+// sum q) combined as (s0 + s1) + (s2 + s3), the order of the warp-tile
+// kernel above, so both give the network's rounding points in the same
+// binary32 error model.  Training keeps the warp-tile kernels.
+
+constexpr int kTcThreads = 128;  // one sample per thread, one 128-row MMA tile per block
+constexpr int kTcCols = 64;      // TMEM columns of the accumulator (N = 64, f32)
+
+struct TcSmem {
+    alignas(1024) unsigned char A[kTcThreads * kMHid * 2];  // bf16(h1): 128 x 64, K-major core matrices
+    alignas(1024) unsigned char Bw[kMHid * kMHid * 2];      // W2: 64 (N) x 64 (K)
+    float4 l1[kMHid][2];  // per hidden unit: (W1[j][0..3]), (W1[j][4], b1[j], 0, 0)
+    float4 l3[kMHid];     // per hidden unit: (b2[j], W3[0][j], W3[1][j], 0)
+    float b3[kMOut];
+    unsigned long long mbar;
+    unsigned int taddr;
+    int fail;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 f32 columns [col, col + 16) of this warp's 32 TMEM lanes (lane = row of the tile)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// mbarrier phase wait with a time limit; false when it ran out
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (2ll << 30)) return false;  // ~1 s at 2 GHz
+    }
+}
+
+// MODE 0: outputs to Y (pic_mlp_forward); 1, 2: the learned step's
+// correction of an FP64 / FP32 state, kept where the frozen-field energy
+// check allows it.
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads) k_mlp_tc(MlpDev M, LearnedArgs A, const float* __restrict__ X,
+                                                       float* __restrict__ Y, long long n) {
+    __shared__ TcSmem S;
+    extern __shared__ float s_tab[];  // binary32 field tables of the energy check (MODE 2, Poisson)
+    const int t = threadIdx.x, warp = t >> 5;
+    // W2 as the B operand; the CUDA-core layers' weights packed per hidden unit
+    for (int i = t; i < kMHid * kMHid / 8; i += kTcThreads) {
+        const int nrow = i >> 3, kb = i & 7;  // 8 consecutive k of output row nrow
+        *reinterpret_cast<uint4*>(S.Bw + tc_kmajor_offset(nrow, kb * 8)) =
+            *reinterpret_cast<const uint4*>(M.W2b + nrow * kMHid + kb * 8);
+    }
+    if (t < kMHid) {
+        const float* w1 = M.small + sW1 + t * kMIn;
+        S.l1[t][0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+        S.l1[t][1] = make_float4(w1[4], M.small[sb1 + t], 0.f, 0.f);
+        S.l3[t] = make_float4(M.small[sb2 + t], M.small[sW3 + t], M.small[sW3 + kMHid + t], 0.f);
+    }
+    if (t < kMOut) S.b3[t] = M.small[sb3 + t];
+    if (MODE == 2 && A.tab_f)
+        for (int i = t; i < 3 * (A.n_cells + 1); i += kTcThreads) s_tab[i] = A.tab_f[i];
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.taddr)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = S.taddr;
+    const uint32_t idesc = tc_idesc_bf16_f32(kTcThreads, kMHid);
+    const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.Bw), mbar = smem_u32(&S.mbar);
+
     EnergyF32 E32;
     E32.field = A.field;
     E32.eps = (float)A.eps;
@@ -482,81 +583,200 @@ __global__ void __launch_bounds__(kFbThreads) k_learned_apply(MlpDev M, LearnedA
     E32.r_min = (float)A.r_min;
     E32.hr = (float)A.hr;
     E32.inv_hr = (float)A.inv_hr;
+    const float* tab_f = (MODE == 2 && A.tab_f) ? s_tab : nullptr;
     E32.E = tab_f;
     E32.slope = tab_f ? tab_f + (A.n_cells + 1) : nullptr;
     E32.psi = tab_f ? tab_f + 2 * (A.n_cells + 1) : nullptr;
-    if (A.field == PIC_FIELD_POISSON && !A.tab_f) E32.field = -1;  // no tables: every particle in FP64
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-    const long long n = A.n, tiles = (n + 15) / 16;
+    if (A.field == PIC_FIELD_POISSON && !tab_f) E32.field = -1;  // no tables: every particle in FP64
+
     unsigned int fallback = 0;
-    for (long long tile = (long long)blockIdx.x * (kFbThreads / 32) + w; tile < tiles;
-         tile += (long long)gridDim.x * (kFbThreads / 32)) {
-        double yp[2][2];
-        bool valid[2];
-        float x[2][kMIn];
+    uint32_t parity = 0;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long s = tile * kTcThreads + t;
+        const bool valid = s < n;
+        float x[kMIn];
+        if (MODE == 0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long s = tile * 16 + g + 8 * h;
-            valid[h] = s < n;
-            if (PREC == 0) {
-                const double2 v = valid[h] ? ((const double2*)A.y_prev)[s] : make_double2(0.0, 0.0);
-                yp[h][0] = v.x;
-                yp[h][1] = v.y;
+            for (int i = 0; i < kMIn; ++i) x[i] = valid ? X[s * kMIn + i] : 0.f;
+        } else {
+            if (MODE == 1) {
+                const double2 v = valid ? ((const double2*)A.y_prev)[s] : make_double2(0.0, 0.0);
+                x[0] = (float)v.x;
+                x[1] = (float)v.y;
             } else {
-                const float2 v = valid[h] ? ((const float2*)A.y_prev)[s] : make_float2(0.f, 0.f);
-                yp[h][0] = v.x;
-                yp[h][1] = v.y;
+                const float2 v = valid ? ((const float2*)A.y_prev)[s] : make_float2(0.f, 0.f);
+                x[0] = v.x;
+                x[1] = v.y;
             }
-            x[h][0] = (float)yp[h][0];
-            x[h][1] = (float)yp[h][1];
-            x[h][2] = A.in_sin;
-            x[h][3] = A.in_cos;
-            x[h][4] = A.in_dt;
+            x[2] = A.in_sin;
+            x[3] = A.in_cos;
+            x[4] = A.in_dt;
         }
-        Tile T;
-        tile_forward(S, x, T);
-        if (t < 2) {
-            // row g (t = 0) or g + 8 (t = 1); selects rather than T.out[t]:
-            // an index that depends on the lane would move the tile to local memory
-            const int h = t;
-            const long long s = tile * 16 + g + 8 * h;
-            const float o0 = h ? T.out[1][0] : T.out[0][0], o1 = h ? T.out[1][1] : T.out[0][1];
-            const bool ok = h ? valid[1] : valid[0];
-            const float dRf = A.scale_R * o0, dVf = A.scale_V * o1;
-            if (ok && (dRf != 0.0f || dVf != 0.0f)) {
-                double Rp, Vp, Rl, Vl;
-                int dec = -1;
-                if (PREC == 0) {
-                    const double2 pl = ((const double2*)A.y)[s];
-                    Rp = pl.x;
-                    Vp = pl.y;
-                    Rl = pl.x + (double)dRf;
-                    Vl = pl.y + (double)dVf;
-                } else {
-                    const float2 pl = ((const float2*)A.y)[s];
-                    const float R1 = pl.x + dRf, V1 = pl.y + dVf;
-                    Rp = pl.x;
-                    Vp = pl.y;
-                    Rl = (double)R1;
-                    Vl = (double)V1;
-                    // binary32 where it provably gives the FP64 decision
-                    dec = energy_check_f32(E32, pl.x, pl.y, R1, V1);
+        // layer 1 + GELU into the A operand: row t, 8 columns (one 16-byte
+        // core-matrix row) per pass; the pass loop stays rolled, since 64
+        // inlined erfc evaluations per layer overflow the instruction cache
+#pragma unroll 1
+        for (int kb = 0; kb < kMHid / 8; ++kb) {
+            unsigned int packed[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float h[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int col = kb * 8 + e + q;
+                    const float4 wa = S.l1[col][0], wb = S.l1[col][1];
+                    float z = wb.y;
+                    z = fmaf(wa.x, x[0], z);
+                    z = fmaf(wa.y, x[1], z);
+                    z = fmaf(wa.z, x[2], z);
+                    z = fmaf(wa.w, x[3], z);
+                    z = fmaf(wb.x, x[4], z);
+                    h[q] = gelu_f(z);
                 }
-                // the plain step judges: the correction may move the frozen-field
-                // energy away from the plain step's by at most tol |H|
-                const bool keep = dec >= 0 ? dec == 1 : frozen_keep_fp64(A, Rp, Vp, Rl, Vl);
-                if (keep) {
-                    if (PREC == 0) ((double2*)A.y)[s] = make_double2(Rl, Vl);
-                    else ((float2*)A.y)[s] = make_float2((float)Rl, (float)Vl);
-                } else {
-                    ++fallback;
-                }
+                packed[e >> 1] = pack_bf16(h[0], h[1]);
             }
+            *reinterpret_cast<uint4*>(S.A + tc_kmajor_offset(t, kb * 8)) =
+                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+        // the generic-proxy writes of A become visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < kMHid / 16; ++ks) {
+                const uint64_t ad = tc_smem_desc(a_base + ks * 2 * kTcLbo, kTcLbo, kTcSbo);
+                const uint64_t bd = tc_smem_desc(b_base + ks * 2 * kTcLbo, kTcLbo, kTcSbo);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)ks)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                         : "memory");
+        }
+        if (!tc_wait(mbar, parity)) S.fail = 1;
+        parity ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (S.fail) break;
+        // z2 = D + b2 of this thread's row, GELU, bf16, output layer
+        float acc[kMOut][4];
+#pragma unroll
+        for (int o = 0; o < kMOut; ++o)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll 1
+        for (int cb = 0; cb < kMHid / 16; ++cb) {
+            float d[16];
+            tc_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int q = (i & 7) >> 1;
+                const float4 w = S.l3[cb * 16 + i];
+                const float h2 = round_bf16(gelu_f(d[i] + w.x));
+                acc[0][q] = fmaf(w.y, h2, acc[0][q]);
+                acc[1][q] = fmaf(w.z, h2, acc[1][q]);
+            }
+        }
+        tc_fence_before();  // this tile's TMEM reads come before the next tile's MMA
+        float out[kMOut];
+#pragma unroll
+        for (int o = 0; o < kMOut; ++o) out[o] = ((acc[o][0] + acc[o][1]) + (acc[o][2] + acc[o][3])) + S.b3[o];
+        if (!valid) continue;
+        if (MODE == 0) {
+            Y[s * kMOut] = out[0];
+            Y[s * kMOut + 1] = out[1];
+            continue;
+        }
+        const float dRf = A.scale_R * out[0], dVf = A.scale_V * out[1];
+        if (dRf == 0.0f && dVf == 0.0f) continue;
+        double Rp, Vp, Rl, Vl;
+        int dec = -1;
+        if (MODE == 1) {
+            const double2 pl = ((const double2*)A.y)[s];
+            Rp = pl.x;
+            Vp = pl.y;
+            Rl = pl.x + (double)dRf;
+            Vl = pl.y + (double)dVf;
+        } else {
+            const float2 pl = ((const float2*)A.y)[s];
+            const float R1 = pl.x + dRf, V1 = pl.y + dVf;
+            Rp = pl.x;
+            Vp = pl.y;
+            Rl = (double)R1;
+            Vl = (double)V1;
+            // binary32 where it provably gives the FP64 decision
+            dec = energy_check_f32(E32, pl.x, pl.y, R1, V1);
+        }
+        // the plain step judges: the correction may move the frozen-field
+        // energy away from the plain step's by at most tol |H|
+        const bool keep = dec >= 0 ? dec == 1 : frozen_keep_fp64(A, Rp, Vp, Rl, Vl);
+        if (keep) {
+            if (MODE == 1) ((double2*)A.y)[s] = make_double2(Rl, Vl);
+            else ((float2*)A.y)[s] = make_float2((float)Rl, (float)Vl);
+        } else {
+            ++fallback;
         }
     }
+    if (MODE != 0) {
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) fallback += __shfl_xor_sync(0xffffffffu, fallback, d);
-    if (lane == 0 && fallback) atomicAdd(A.n_fallback, (unsigned long long)fallback);
+        for (int d = 16; d >= 1; d >>= 1) fallback += __shfl_xor_sync(0xffffffffu, fallback, d);
+        if ((t & 31) == 0 && fallback) atomicAdd(A.n_fallback, (unsigned long long)fallback);
+    }
+    if (t == 0 && S.fail) atomicExch(M.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+    }
+}
+
+// Blocks of k_mlp_tc resident on one SM, from its registers, its shared
+// memory and its 64 tensor-memory columns (512 per SM).  The runtime's
+// occupancy query answers 1 for this kernel, which would leave 7 of every 8
+// warp slots it could use empty.
+static int tc_blocks_per_sm(const void* fn, size_t dyn_smem) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
+        return 1;
+    const int regs_block = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;  // allocated per warp in units of 8 per thread
+    int k = 512 / kTcCols;
+    k = std::min(k, 2048 / kTcThreads);
+    if (regs_block > 0) k = std::min(k, regs_sm / regs_block);
+    k = std::min(k, (int)((size_t)smem_sm / (fa.sharedSizeBytes + dyn_smem + (size_t)resv)));
+    return k < 1 ? 1 : k;
+}
+
+// Launch of the tensor-core inference over n samples: as many blocks as are
+// resident at once, no more blocks than tiles.
+cudaError_t launch_mlp_tc(const MlpDev& D, const LearnedArgs& A, int mode, const float* X, float* Y, long long n,
+                          int sm_count, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const size_t smem = (mode == 2 && A.tab_f) ? sizeof(float) * 3 * (size_t)(A.n_cells + 1) : 0;
+    void* fn = mode == 0 ? (void*)k_mlp_tc<0> : mode == 1 ? (void*)k_mlp_tc<1> : (void*)k_mlp_tc<2>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && smem > 48 * 1024)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int per_sm = tc_blocks_per_sm(fn, smem);
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    const long long cap = (long long)sm_count * per_sm;
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    if (mode == 0) k_mlp_tc<0><<<grid, kTcThreads, smem, st>>>(D, A, X, Y, n);
+    else if (mode == 1) k_mlp_tc<1><<<grid, kTcThreads, smem, st>>>(D, A, X, Y, n);
+    else k_mlp_tc<2><<<grid, kTcThreads, smem, st>>>(D, A, X, Y, n);
+    return cudaGetLastError();
 }
 
 __global__ void k_psi_nodes(const double* __restrict__ E, int n_cells, double hr, double* __restrict__ psi,
@@ -586,7 +806,7 @@ cudaError_t launch_psi_nodes(const double* E, int n_cells, double hr, double* ps
     return cudaGetLastError();
 }
 
-// psi at n positions: the same psi_at the energy check of k_learned_apply uses.
+// psi at n positions: the same psi_at the learned step's FP64 energy check uses.
 __global__ void k_psi_eval(LearnedArgs A, const double* __restrict__ R, double* __restrict__ out) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += stride) out[i] = psi_at(A, R[i]);
@@ -690,23 +910,22 @@ namespace pic {
 cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_count, cudaStream_t st,
                                  long long* launches) {
     if (A.n == 0) return cudaSuccess;
-    const long long tiles = (A.n + 15) / 16;
-    long long g = (tiles + 3) / 4;
-    // one wave: as many blocks as are resident at once (the kernel strides over the tiles)
-    auto fn = A.prec == 0 ? k_learned_apply<0> : k_learned_apply<1>;
-    const size_t smem = A.tab_f ? sizeof(float) * 3 * (size_t)(A.n_cells + 1) : 0;
-    if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFbThreads, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const long long cap = (long long)sm_count * per_sm;
-    const int grid = (int)(g < 1 ? 1 : (g < cap ? g : cap));
-    fn<<<grid, kFbThreads, smem, st>>>(m->D, A);
+    const cudaError_t e = launch_mlp_tc(m->D, A, A.prec == 0 ? 1 : 2, nullptr, nullptr, A.n, sm_count, st);
     if (launches) ++*launches;
-    return cudaGetLastError();
+    return e;
+}
+
+// PIC_ERR_TIMEOUT (and the flag cleared) when a tensor-core wait of the
+// inference kernel ran out of time since the last call; synchronises st.
+int mlp_take_error(const pic_mlp* m, cudaStream_t st) {
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, m->D.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PIC_ERR_NO_MEMORY : PIC_ERR_CUDA;
+    if (!err) return PIC_OK;
+    e = cudaMemsetAsync(m->D.err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PIC_ERR_TIMEOUT : PIC_ERR_CUDA;
 }
 }  // namespace pic
 
@@ -746,6 +965,8 @@ int pic_mlp_create(int64_t max_batch, void* stream, pic_mlp** out) {
     if (e == cudaSuccess) e = mlp_alloc(m, &D.grad_part, (size_t)pic::kWgMaxBlocks * pic::kMParams);
     if (e == cudaSuccess) e = mlp_alloc(m, &D.grad, pic::kMParams);
     if (e == cudaSuccess) e = mlp_alloc(m, &D.loss, 1);
+    if (e == cudaSuccess) e = mlp_alloc(m, &D.err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D.err, 0, sizeof(int), m->st);
     if (e == cudaSuccess) e = cudaMallocHost(&m->loss_host, sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(D.master, 0, sizeof(float) * pic::kMParams, m->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(D.m, 0, sizeof(float) * pic::kMParams, m->st);
@@ -790,10 +1011,11 @@ int pic_mlp_get_weights(pic_mlp* m, float* w, int ptr_kind) {
 int pic_mlp_forward(pic_mlp* m, int64_t n, const float* X_dev, float* Y_dev) {
     if (!m || n < 0 || (n > 0 && (!X_dev || !Y_dev))) return PIC_ERR_INVALID_ARG;
     if (n == 0) return PIC_OK;
-    pic::k_mlp_fwd_bwd<<<fb_grid(m, n), pic::kFbThreads, 0, m->st>>>(m->D, X_dev, nullptr, Y_dev, n, 0, 1, n, 1.0f);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
-    return mlp_map(e);
+    pic::LearnedArgs A;
+    std::memset(&A, 0, sizeof(A));
+    const cudaError_t e = pic::launch_mlp_tc(m->D, A, 0, X_dev, Y_dev, n, m->sm_count, m->st);
+    if (e != cudaSuccess) return mlp_map(e);
+    return pic::mlp_take_error(m, m->st);
 }
 
 int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_dev, float* grad, float* loss,

@@ -222,6 +222,10 @@ struct LearnedArgs {
 };
 cudaError_t launch_learned_apply(const pic_mlp* m, const LearnedArgs& A, int sm_count, cudaStream_t st,
                                  long long* launches);
+// PIC_ERR_TIMEOUT when a tensor-core wait of the network's inference kernel
+// ran out of time since the last call (the flag is then cleared), else
+// PIC_OK; synchronises st.
+int mlp_take_error(const pic_mlp* m, cudaStream_t st);
 // psi at the nodes from E at the nodes (trapezoid of the piecewise-linear field);
 // with tab_f (3 (n_cells+1) floats, may be null) also the binary32 copies of
 // E_j, (E_{j+1} - E_j)/h_r and psi_j for the energy check of the FP32 form.
