@@ -250,12 +250,12 @@ def roofline_of(prm, wl_name, n, K, kern_ms, scheme=None, timed_K=None, win_n=0)
     if prm.precision == 1:
         bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * n * K
         achieved = bytes_ / (kern_ms / 1e3)
-        peak = measured_hbm_peak()
+        peak, peak_src = measured_hbm_peak()
         return {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": kernel_traffic(n, wl_name),
                 "kernel": "k_window32_coop (FP32 form, one launch per macro step)",
                 "kernel_ms": kern_ms, "fine_steps_per_launch": K, "algorithmic_bytes_per_launch": bytes_,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth), of measured"}
+                "peak_source": peak_src}
     if scheme is not None:
         # the comparator's step runs several windows (the fine solves over P
         # and o, and for the modified scheme the period detection); its
@@ -559,7 +559,7 @@ def measure_batch(wl_name, steps, warmup, with_e2e=True):
     b.close()
     mean_ms = float(np.mean(step_ms))
     bytes_ = BYTES_PER_PARTICLE_FINE_STEP_F32 * float(np.sum(sizes * Ks))
-    peak = measured_hbm_peak()
+    peak, peak_src = measured_hbm_peak()
     achieved = bytes_ / (mean_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
@@ -573,7 +573,7 @@ def measure_batch(wl_name, steps, warmup, with_e2e=True):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_window32_batch (all beams, one cooperative launch per macro step)",
                      "kernel_ms": mean_ms, "algorithmic_bytes_per_launch": bytes_,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth), of measured"},
+                     "peak_source": peak_src},
         "gpu_launches": int(launches), "wall_s": wall, "clocks": clk.summary(),
         "error_vs_oracle": "every beam bit-identical to the FP32 form run alone, and every beam of a mixed batch "
                            "within the binary32 bound of the FP64 oracle (tests/test_gpu_batch.py)",
@@ -696,9 +696,21 @@ def learned_errors(prm, wl, net, out_scale):
     return out
 
 
-def measured_hbm_peak() -> float:
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-        return float(json.load(fh)["hbm_gbs"]) * 1e9
+FALLBACK_HBM_GBS = 6800.0  # one earlier copy-bandwidth measurement on a GB300
+
+
+def measured_hbm_peak():
+    """HBM peak in B/s and where it comes from: the measured copy bandwidth
+    of the GB300s when MEASURED_PEAKS.json is present, else the
+    fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return (float(json.load(fh)["hbm_gbs"]) * 1e9,
+                    "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth), of measured")
+    except (OSError, ValueError, KeyError, TypeError):
+        return (FALLBACK_HBM_GBS * 1e9,
+                "6.8 TB/s, an earlier copy-bandwidth measurement on a GB300 (no MEASURED_PEAKS.json), of fallback")
 
 
 def error_vs_fp64(workload: str):
