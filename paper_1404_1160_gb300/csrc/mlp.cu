@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "energy_check.cuh"
+#include "gelu_fast.cuh"
 #include "pic_internal.h"
 #include "tc_desc.cuh"
 
@@ -70,7 +71,6 @@ struct MlpDev {
 
 // ------------------------------------------------------------ device math
 
-__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * erfcf(-u * 0.70710678118654752f); }
 __device__ __forceinline__ float gelu_d(float u) {
     return 0.5f * erfcf(-u * 0.70710678118654752f) + u * 0.39894228040143268f * expf(-0.5f * u * u);
 }
@@ -494,6 +494,7 @@ struct TcSmem {
     float4 l1[kMHid][2];  // per hidden unit: (W1[j][0..3]), (W1[j][4], b1[j], 0, 0)
     float4 l3[kMHid];     // per hidden unit: (b2[j], W3[0][j], W3[1][j], 0)
     float b3[kMOut];
+    float4 gtab[kGeluSeg + 1];  // segment table of gelu_for_bf16
     unsigned long long mbar;
     unsigned int taddr;
     int fail;
@@ -555,6 +556,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_tc(MlpDev M, LearnedArgs A, 
         S.l3[t] = make_float4(M.small[sb2 + t], M.small[sW3 + t], M.small[sW3 + kMHid + t], 0.f);
     }
     if (t < kMOut) S.b3[t] = M.small[sb3 + t];
+    if (t <= kGeluSeg) S.gtab[t] = make_float4(c_gelu_tab[t][0], c_gelu_tab[t][1], c_gelu_tab[t][2], c_gelu_tab[t][3]);
     if (MODE == 2 && A.tab_f)
         for (int i = t; i < 3 * (A.n_cells + 1); i += kTcThreads) s_tab[i] = A.tab_f[i];
     if (t == 0) {
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_tc(MlpDev M, LearnedArgs A, 
                     z = fmaf(wa.z, x[2], z);
                     z = fmaf(wa.w, x[3], z);
                     z = fmaf(wb.x, x[4], z);
-                    h[q] = gelu_f(z);
+                    h[q] = gelu_for_bf16(z, S.gtab);  // rounded to bf16 by pack_bf16
                 }
                 packed[e >> 1] = pack_bf16(h[0], h[1]);
             }
@@ -678,7 +680,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_tc(MlpDev M, LearnedArgs A, 
             for (int i = 0; i < 16; ++i) {
                 const int q = (i & 7) >> 1;
                 const float4 w = S.l3[cb * 16 + i];
-                const float h2 = round_bf16(gelu_f(d[i] + w.x));
+                const float h2 = round_bf16(gelu_for_bf16(d[i] + w.x, S.gtab));
                 acc[0][q] = fmaf(w.y, h2, acc[0][q]);
                 acc[1][q] = fmaf(w.z, h2, acc[1][q]);
             }
