@@ -1,7 +1,7 @@
 // mlp.cu -- the network of the learned stepper: a 5-64-64-2 GELU perceptron
-// with bfloat16 weights and FP32 accumulation on the tensor cores: inference
-// (and the learned step's correction) with tcgen05.mma into tensor memory,
-// training with warp-level mma.sync m16n8k16 (bf16 x bf16 -> f32).  The paper has no
+// with bfloat16 weights and FP32 accumulation, its 64 x 64 products on the
+// 5th-generation tensor cores (tcgen05.mma, bf16 x bf16 -> f32 in tensor
+// memory) for inference, the learned step's correction and training.  The paper has no
 // learned component; the network corrects one macro step of the improved ETD
 // scheme (Algorithm ETDFSSModAlgo) and is defined, with its rounding points,
 // as:
@@ -17,10 +17,11 @@
 //   dout = (out - y) / B, dW3 = dout^T bf16(h2), db3 = sum dout,
 //   dz2 = (dout W3) gelu'(z2), dW2 = bf16(dz2)^T bf16(h1), db2 = sum dz2,
 //   dz1 = (bf16(dz2) W2) gelu'(z1), dW1 = dz1^T x, db1 = sum dz1.
-// The per-sample part (forward, dz1, dz2) runs one warp per 16 samples; the
-// weight gradients are reduced over the batch by a second kernel (dW2 on the
-// tensor cores) into per-block partials, which a third kernel sums in a fixed
-// order before the Adam update, so training is reproducible bit for bit.
+// The per-sample part (forward, dz1, dz2) runs one sample per thread and 128
+// per MMA tile; the weight gradients are reduced over the batch by a second
+// kernel (dW2 on the tensor cores, the samples as the reduction dimension)
+// into per-block partials, which a third kernel sums in a fixed order before
+// the Adam update, so training is reproducible bit for bit.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -45,9 +46,7 @@ static_assert(kMParams == 4674, "parameter count");
 constexpr int sW1 = 0, sb1 = sW1 + kMHid * kMIn, sb2 = sb1 + kMHid, sW3 = sb2 + kMHid, sb3 = sW3 + kMOut * kMHid,
               kMSmall = sb3 + kMOut;
 
-constexpr int kFbThreads = 128;  // 4 warps, 16 samples each per tile
-constexpr int kWgThreads = 128;  // weight-gradient blocks
-constexpr int kWgTile = 64;      // samples per staged tile
+constexpr int kWgTile = 64;      // samples per staged tile of the weight gradients
 constexpr int kWgMaxBlocks = 256;
 
 struct MlpDev {
@@ -80,311 +79,11 @@ __device__ __forceinline__ unsigned int pack_bf16(float lo, float hi) {
 }
 __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// D += A B for one 16x8x16 tile (A row-major 16x16, B col-major 16x8, bf16; D f32).
-__device__ __forceinline__ void mma_bf16(float c[4], unsigned int a0, unsigned int a1, unsigned int a2, unsigned int a3,
-                                         unsigned int b0, unsigned int b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ unsigned int ld_bf16x2(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned int*>(p); }
-
-// Weights a block keeps in shared memory.
-struct MlpSmem {
-    __nv_bfloat16 W2b[kMHid * kMHid];
-    __nv_bfloat16 W2Tb[kMHid * kMHid];
-    float small[kMSmall];
-};
-
-__device__ __forceinline__ void load_weights(const MlpDev& M, MlpSmem& S, bool need_T) {
-    const unsigned int* src = reinterpret_cast<const unsigned int*>(M.W2b);
-    unsigned int* dst = reinterpret_cast<unsigned int*>(S.W2b);
-    for (int i = threadIdx.x; i < kMHid * kMHid / 2; i += blockDim.x) dst[i] = src[i];
-    if (need_T) {
-        src = reinterpret_cast<const unsigned int*>(M.W2Tb);
-        dst = reinterpret_cast<unsigned int*>(S.W2Tb);
-        for (int i = threadIdx.x; i < kMHid * kMHid / 2; i += blockDim.x) dst[i] = src[i];
-    }
-    for (int i = threadIdx.x; i < kMSmall; i += blockDim.x) S.small[i] = M.small[i];
-    __syncthreads();
-}
-
-// Per-warp forward pass of 16 samples.  Thread (g = lane/4, t = lane%4)
-// holds rows g and g+8 (h = 0, 1) and, for every 8-column tile nt, columns
-// nt*8 + 2t + e (e = 0, 1): element [nt][2h + e] of z1 / z2 (the m16n8
-// accumulator layout, which is also the A-operand layout of the next GEMM).
-struct Tile {
-    float z1[8][4];
-    float z2[8][4];
-    float out[2][2];
-};
-
-__device__ __forceinline__ void tile_forward(const MlpSmem& S, const float x[2][kMIn], Tile& T) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    // layer 1 on the CUDA cores
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int col = nt * 8 + 2 * t + e;
-            const float* w = S.small + sW1 + col * kMIn;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float z = S.small[sb1 + col];
-#pragma unroll
-                for (int i = 0; i < kMIn; ++i) z = fmaf(w[i], x[h][i], z);
-                T.z1[nt][2 * h + e] = z;
-            }
-        }
-    }
-    // layer 2 on the tensor cores: A = bf16(gelu(z1)) (16 x 64), B = W2^T
-    unsigned int a[4][4];
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        a[kb][0] = pack_bf16(gelu_f(T.z1[2 * kb][0]), gelu_f(T.z1[2 * kb][1]));
-        a[kb][1] = pack_bf16(gelu_f(T.z1[2 * kb][2]), gelu_f(T.z1[2 * kb][3]));
-        a[kb][2] = pack_bf16(gelu_f(T.z1[2 * kb + 1][0]), gelu_f(T.z1[2 * kb + 1][1]));
-        a[kb][3] = pack_bf16(gelu_f(T.z1[2 * kb + 1][2]), gelu_f(T.z1[2 * kb + 1][3]));
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-        const __nv_bfloat16* wrow = S.W2b + (nt * 8 + g) * kMHid + 2 * t;
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb)
-            mma_bf16(c, a[kb][0], a[kb][1], a[kb][2], a[kb][3], ld_bf16x2(wrow + kb * 16), ld_bf16x2(wrow + kb * 16 + 8));
-#pragma unroll
-        for (int q = 0; q < 4; ++q) T.z2[nt][q] = c[q] + S.small[sb2 + nt * 8 + 2 * t + (q & 1)];
-    }
-    // layer 3 on the CUDA cores, reduced over the four threads of a row group
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-#pragma unroll
-        for (int o = 0; o < kMOut; ++o) {
-            float s = 0.f;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                for (int e = 0; e < 2; ++e)
-                    s = fmaf(S.small[sW3 + o * kMHid + nt * 8 + 2 * t + e], round_bf16(gelu_f(T.z2[nt][2 * h + e])), s);
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            T.out[h][o] = s + S.small[sb3 + o];
-        }
-    }
-}
-
 // Sample index of batch row s: ((first + s) * mul) mod n_data (a permutation
 // of the data set when mul is coprime with n_data).
 __device__ __forceinline__ long long sample_index(long long s, long long first, long long mul, long long n_data) {
     return (long long)(((unsigned long long)(first + s) % (unsigned long long)n_data) * (unsigned long long)mul %
                        (unsigned long long)n_data);
-}
-
-// ------------------------------------------------------------ kernels
-
-// Inference (Y != nullptr, T == nullptr) or the per-sample part of training
-// (T != nullptr): one warp per 16 batch rows, grid-stride over tiles.
-__global__ void __launch_bounds__(kFbThreads) k_mlp_fwd_bwd(MlpDev M, const float* __restrict__ X,
-                                                            const float* __restrict__ Y, float* __restrict__ out,
-                                                            long long B, long long first, long long mul,
-                                                            long long n_data, float invB) {
-    __shared__ MlpSmem S;
-    __shared__ float s_loss[kFbThreads / 32];
-    const bool train = Y != nullptr;
-    load_weights(M, S, train);
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-    const long long tiles = (B + 15) / 16;
-    float loss = 0.f;
-    for (long long tile = (long long)blockIdx.x * (kFbThreads / 32) + w; tile < tiles;
-         tile += (long long)gridDim.x * (kFbThreads / 32)) {
-        long long s_row[2];
-        bool valid[2];
-        long long idx[2];
-        float x[2][kMIn];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            s_row[h] = tile * 16 + g + 8 * h;
-            valid[h] = s_row[h] < B;
-            idx[h] = valid[h] ? sample_index(s_row[h], first, mul, n_data) : 0;
-#pragma unroll
-            for (int i = 0; i < kMIn; ++i) x[h][i] = valid[h] ? X[idx[h] * kMIn + i] : 0.f;
-        }
-        Tile T;
-        tile_forward(S, x, T);
-        if (!train) {
-            if (t == 0) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (valid[h]) {
-                        out[s_row[h] * kMOut] = T.out[h][0];
-                        out[s_row[h] * kMOut + 1] = T.out[h][1];
-                    }
-            }
-            continue;
-        }
-        // ---- backward of this tile
-        float dout[2][kMOut];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int o = 0; o < kMOut; ++o) {
-                const float d = valid[h] ? T.out[h][o] - Y[idx[h] * kMOut + o] : 0.f;
-                if (t == 0) loss = fmaf(d, d, loss);
-                dout[h][o] = d * invB;
-            }
-        // dz2 = (dout W3) gelu'(z2), kept in the accumulator layout
-        float dz2[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int col = nt * 8 + 2 * t + (q & 1), h = q >> 1;
-                const float dh = fmaf(S.small[sW3 + kMHid + col], dout[h][1], S.small[sW3 + col] * dout[h][0]);
-                dz2[nt][q] = dh * gelu_d(T.z2[nt][q]);
-            }
-        // per-sample records for the weight gradients
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (!valid[h]) continue;
-            const long long s = s_row[h];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = nt * 8 + 2 * t;
-                *reinterpret_cast<float2*>(M.dz2 + s * kMHid + col) = make_float2(dz2[nt][2 * h], dz2[nt][2 * h + 1]);
-                *reinterpret_cast<__nv_bfloat162*>(M.h1b + s * kMHid + col) =
-                    __floats2bfloat162_rn(gelu_f(T.z1[nt][2 * h]), gelu_f(T.z1[nt][2 * h + 1]));
-                *reinterpret_cast<__nv_bfloat162*>(M.h2b + s * kMHid + col) =
-                    __floats2bfloat162_rn(gelu_f(T.z2[nt][2 * h]), gelu_f(T.z2[nt][2 * h + 1]));
-            }
-            if (t == 0) {
-                M.dout[s * kMOut] = dout[h][0];
-                M.dout[s * kMOut + 1] = dout[h][1];
-#pragma unroll
-                for (int i = 0; i < kMIn; ++i) M.xs[s * kMIn + i] = x[h][i];
-            }
-        }
-        // dh1 = bf16(dz2) W2 on the tensor cores: A = bf16(dz2) (16 x 64), B[j][k] = W2[j][k]
-        unsigned int a[4][4];
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            a[kb][0] = pack_bf16(dz2[2 * kb][0], dz2[2 * kb][1]);
-            a[kb][1] = pack_bf16(dz2[2 * kb][2], dz2[2 * kb][3]);
-            a[kb][2] = pack_bf16(dz2[2 * kb + 1][0], dz2[2 * kb + 1][1]);
-            a[kb][3] = pack_bf16(dz2[2 * kb + 1][2], dz2[2 * kb + 1][3]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const __nv_bfloat16* wrow = S.W2Tb + (nt * 8 + g) * kMHid + 2 * t;
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb)
-                mma_bf16(c, a[kb][0], a[kb][1], a[kb][2], a[kb][3], ld_bf16x2(wrow + kb * 16),
-                         ld_bf16x2(wrow + kb * 16 + 8));
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (!valid[h]) continue;
-                const int col = nt * 8 + 2 * t;
-                *reinterpret_cast<float2*>(M.dz1 + s_row[h] * kMHid + col) =
-                    make_float2(c[2 * h] * gelu_d(T.z1[nt][2 * h]), c[2 * h + 1] * gelu_d(T.z1[nt][2 * h + 1]));
-            }
-        }
-    }
-    if (!train) return;
-    // loss partial of this block (fixed reduction order)
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, d);
-    if (lane == 0) s_loss[w] = loss;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int i = 0; i < kFbThreads / 32; ++i) s += s_loss[i];
-        M.loss_part[blockIdx.x] = 0.5f * s * invB;
-    }
-}
-
-// Weight gradients of a batch: block b sums samples [b chunk, (b+1) chunk)
-// into grad_part[b].  dW2 = bf16(dz2)^T h1b runs on the tensor cores: warp w
-// owns rows j = 16w..16w+15 of dW2 and all 64 columns k; a staged tile of 64
-// samples is the reduction dimension (4 k16 steps).
-__global__ void __launch_bounds__(kWgThreads) k_mlp_wgrad(MlpDev M, long long B, long long chunk) {
-    __shared__ __nv_bfloat16 T2[kMHid][kWgTile + 8];  // bf16(dz2)^T: [j][s] (padded rows)
-    __shared__ __nv_bfloat16 H1[kMHid][kWgTile + 8];  // h1b^T: [k][s]
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-    const long long s_begin = (long long)blockIdx.x * chunk;
-    const long long s_end = s_begin + chunk < B ? s_begin + chunk : B;
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
-    for (long long s0 = s_begin; s0 < s_end; s0 += kWgTile) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < kWgTile * kMHid; idx += blockDim.x) {
-            const int s = idx / kMHid, j = idx % kMHid;
-            const long long ss = s0 + s;
-            const bool ok = ss < s_end;
-            T2[j][s] = __float2bfloat16_rn(ok ? M.dz2[ss * kMHid + j] : 0.f);
-            H1[j][s] = ok ? M.h1b[ss * kMHid + j] : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < kWgTile / 16; ++ks) {
-            const int c0 = ks * 16 + 2 * t;
-            const unsigned int a0 = ld_bf16x2(&T2[16 * w + g][c0]);
-            const unsigned int a1 = ld_bf16x2(&T2[16 * w + g + 8][c0]);
-            const unsigned int a2 = ld_bf16x2(&T2[16 * w + g][c0 + 8]);
-            const unsigned int a3 = ld_bf16x2(&T2[16 * w + g + 8][c0 + 8]);
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-                mma_bf16(acc[nt], a0, a1, a2, a3, ld_bf16x2(&H1[nt * 8 + g][c0]), ld_bf16x2(&H1[nt * 8 + g][c0 + 8]));
-        }
-    }
-    float* part = M.grad_part + (size_t)blockIdx.x * kMParams;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = 16 * w + g + 8 * (q >> 1), k = nt * 8 + 2 * t + (q & 1);
-            part[oW2 + j * kMHid + k] = acc[nt][q];
-        }
-    // the small gradients on the CUDA cores, one column per thread
-    const int tid = threadIdx.x;
-    if (tid < kMHid) {
-        const int j = tid;
-        float gw[kMIn] = {0.f, 0.f, 0.f, 0.f, 0.f}, gb1 = 0.f, gb2 = 0.f;
-        for (long long s = s_begin; s < s_end; ++s) {
-            const float d1 = M.dz1[s * kMHid + j];
-#pragma unroll
-            for (int i = 0; i < kMIn; ++i) gw[i] = fmaf(d1, M.xs[s * kMIn + i], gw[i]);
-            gb1 += d1;
-            gb2 += M.dz2[s * kMHid + j];
-        }
-#pragma unroll
-        for (int i = 0; i < kMIn; ++i) part[oW1 + j * kMIn + i] = gw[i];
-        part[ob1 + j] = gb1;
-        part[ob2 + j] = gb2;
-    } else {
-        const int j = tid - kMHid;
-        float g0 = 0.f, g1 = 0.f, d0 = 0.f, d1 = 0.f;
-        for (long long s = s_begin; s < s_end; ++s) {
-            const float h = __bfloat162float(M.h2b[s * kMHid + j]);
-            const float o0 = M.dout[s * kMOut], o1 = M.dout[s * kMOut + 1];
-            g0 = fmaf(o0, h, g0);
-            g1 = fmaf(o1, h, g1);
-            d0 += o0;
-            d1 += o1;
-        }
-        part[oW3 + j] = g0;
-        part[oW3 + kMHid + j] = g1;
-        if (j == 0) {
-            part[ob3] = d0;
-            part[ob3 + 1] = d1;
-        }
-    }
 }
 
 struct AdamArgs {
@@ -480,10 +179,10 @@ static __device__ __noinline__ bool frozen_keep_fp64(const LearnedArgs& A, doubl
 // each) against W2 (B operand, 64 x 64) into a 64-column f32 accumulator in
 // tensor memory and commits them to an mbarrier; each warp then reads its 32
 // rows back with tcgen05.ld.  The output layer adds the products of each
-// sample's 64 columns in four partial sums of 16 (columns 8 nt + 2 q + e for
-// sum q) combined as (s0 + s1) + (s2 + s3), the order of the warp-tile
-// kernel above, so both give the network's rounding points in the same
-// binary32 error model.  Training keeps the warp-tile kernels.
+// sample's 64 columns in four fused multiply-add chains of 16 (columns
+// 8 nt + 2 q + e for chain q) combined as (s0 + s1) + (s2 + s3).  Where a
+// GELU is rounded to bfloat16 at once it is evaluated by gelu_for_bf16
+// (gelu_fast.cuh), which rounds exactly as the erfc form does.
 
 constexpr int kTcThreads = 128;  // one sample per thread, one 128-row MMA tile per block
 constexpr int kTcCols = 64;      // TMEM columns of the accumulator (N = 64, f32)
@@ -781,6 +480,357 @@ cudaError_t launch_mlp_tc(const MlpDev& D, const LearnedArgs& A, int mode, const
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ tensor-core training (tcgen05)
+//
+// The per-sample part of a training step: one sample per thread, 128 per
+// block and tile.  Forward as in k_mlp_tc (MMA 1: z2 = bf16(h1) W2^T + b2),
+// then dout = (out - y)/B, dz2 = (dout W3) gelu'(z2), and MMA 2 (same tensor
+// memory, same A buffer): dh1 = bf16(dz2) W2 against W2^T staged as the B
+// operand, dz1 = dh1 gelu'(z1) with z1 recomputed from x.  Every sample
+// leaves its records (x, bf16(h1), bf16(h2), dout, dz2, dz1) for the
+// weight-gradient kernel, every block its loss partial.
+
+struct TcTrainSmem {
+    alignas(1024) unsigned char A[kTcThreads * kMHid * 2];  // bf16(h1), then bf16(dz2): 128 x 64, K-major
+    alignas(1024) unsigned char Bw[kMHid * kMHid * 2];      // W2: N = j, K = k
+    alignas(1024) unsigned char Bt[kMHid * kMHid * 2];      // W2^T: N = k, K = j
+    float4 l1[kMHid][2];
+    float4 l3[kMHid];
+    float b3[kMOut];
+    float4 gtab[kGeluSeg + 1];
+    unsigned long long mbar;
+    unsigned int taddr;
+    int fail;
+    float loss[kTcThreads / 32];
+};
+
+// Thread 0: the four K = 16 MMAs of a K = 64 product into the accumulator at
+// taddr (accumulating onto it when acc), committed to the mbarrier.
+__device__ __forceinline__ void tc_issue_k64(uint32_t taddr, uint32_t a_base, uint32_t b_base, uint32_t idesc,
+                                             bool acc, uint32_t mbar) {
+    tc_fence_after();
+#pragma unroll
+    for (int ks = 0; ks < kMHid / 16; ++ks) {
+        const uint64_t ad = tc_smem_desc(a_base + ks * 2 * kTcLbo, kTcLbo, kTcSbo);
+        const uint64_t bd = tc_smem_desc(b_base + ks * 2 * kTcLbo, kTcLbo, kTcSbo);
+        const uint32_t en = (acc || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(en)
+            : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// A 64 x 64 bf16 matrix (row-major, rows along N) as a K-major B operand.
+__device__ __forceinline__ void tc_stage_b(unsigned char* dst, const __nv_bfloat16* __restrict__ src) {
+    for (int i = threadIdx.x; i < kMHid * kMHid / 8; i += blockDim.x) {
+        const int nrow = i >> 3, kb = i & 7;
+        *reinterpret_cast<uint4*>(dst + tc_kmajor_offset(nrow, kb * 8)) =
+            *reinterpret_cast<const uint4*>(src + nrow * kMHid + kb * 8);
+    }
+}
+
+// Block-wide: MMA issued by thread 0 after the A writes of every thread,
+// then every thread waits for it; false (and the block's fail flag) when
+// the wait ran out of time.
+__device__ __forceinline__ bool tc_block_mma(uint32_t taddr, uint32_t a_base, uint32_t b_base, uint32_t idesc, bool acc,
+                                             uint32_t mbar, uint32_t& parity, int& fail) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) tc_issue_k64(taddr, a_base, b_base, idesc, acc, mbar);
+    if (!tc_wait(mbar, parity)) fail = 1;
+    parity ^= 1u;
+    tc_fence_after();
+    __syncthreads();
+    return !fail;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_mlp_train_tc(MlpDev M, const float* __restrict__ X,
+                                                             const float* __restrict__ Y, long long B, long long first,
+                                                             long long mul, long long n_data, float invB) {
+    __shared__ TcTrainSmem S;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    tc_stage_b(S.Bw, M.W2b);
+    tc_stage_b(S.Bt, M.W2Tb);
+    if (t < kMHid) {
+        const float* w1 = M.small + sW1 + t * kMIn;
+        S.l1[t][0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+        S.l1[t][1] = make_float4(w1[4], M.small[sb1 + t], 0.f, 0.f);
+        S.l3[t] = make_float4(M.small[sb2 + t], M.small[sW3 + t], M.small[sW3 + kMHid + t], 0.f);
+    }
+    if (t < kMOut) S.b3[t] = M.small[sb3 + t];
+    if (t <= kGeluSeg) S.gtab[t] = make_float4(c_gelu_tab[t][0], c_gelu_tab[t][1], c_gelu_tab[t][2], c_gelu_tab[t][3]);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.taddr)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = S.taddr, trow = taddr + ((uint32_t)(warp * 32) << 16);
+    const uint32_t idesc = tc_idesc_bf16_f32(kTcThreads, kMHid);
+    const uint32_t a_base = smem_u32(S.A), mbar = smem_u32(&S.mbar);
+    uint32_t parity = 0;
+    float loss = 0.f;
+    const long long tiles = (B + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long s = tile * kTcThreads + t;
+        const bool valid = s < B;
+        const long long idx = valid ? sample_index(s, first, mul, n_data) : 0;
+        float x[kMIn];
+#pragma unroll
+        for (int i = 0; i < kMIn; ++i) x[i] = valid ? X[idx * kMIn + i] : 0.f;
+        // layer 1 + GELU: the A operand and the h1 record
+#pragma unroll 1
+        for (int kb = 0; kb < kMHid / 8; ++kb) {
+            unsigned int packed[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float h[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int col = kb * 8 + e + q;
+                    const float4 wa = S.l1[col][0], wb = S.l1[col][1];
+                    float z = wb.y;
+                    z = fmaf(wa.x, x[0], z);
+                    z = fmaf(wa.y, x[1], z);
+                    z = fmaf(wa.z, x[2], z);
+                    z = fmaf(wa.w, x[3], z);
+                    z = fmaf(wb.x, x[4], z);
+                    h[q] = gelu_for_bf16(z, S.gtab);
+                }
+                packed[e >> 1] = pack_bf16(h[0], h[1]);
+            }
+            const uint4 v = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            *reinterpret_cast<uint4*>(S.A + tc_kmajor_offset(t, kb * 8)) = v;
+            if (valid) *reinterpret_cast<uint4*>(M.h1b + s * kMHid + kb * 8) = v;
+        }
+        if (!tc_block_mma(taddr, a_base, smem_u32(S.Bw), idesc, false, mbar, parity, S.fail)) break;
+        // output layer (the order of k_mlp_tc) and the h2 record
+        float acc[kMOut][4];
+#pragma unroll
+        for (int o = 0; o < kMOut; ++o)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll 1
+        for (int cb = 0; cb < kMHid / 16; ++cb) {
+            float d[16], h2[16];
+            tc_ld16(trow + (uint32_t)(cb * 16), d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int q = (i & 7) >> 1;
+                const float4 w = S.l3[cb * 16 + i];
+                h2[i] = round_bf16(gelu_for_bf16(d[i] + w.x, S.gtab));
+                acc[0][q] = fmaf(w.y, h2[i], acc[0][q]);
+                acc[1][q] = fmaf(w.z, h2[i], acc[1][q]);
+            }
+            if (valid) {
+                uint4* dst = reinterpret_cast<uint4*>(M.h2b + s * kMHid + cb * 16);
+                dst[0] = make_uint4(pack_bf16(h2[0], h2[1]), pack_bf16(h2[2], h2[3]), pack_bf16(h2[4], h2[5]),
+                                    pack_bf16(h2[6], h2[7]));
+                dst[1] = make_uint4(pack_bf16(h2[8], h2[9]), pack_bf16(h2[10], h2[11]), pack_bf16(h2[12], h2[13]),
+                                    pack_bf16(h2[14], h2[15]));
+            }
+        }
+        float dout[kMOut];
+#pragma unroll
+        for (int o = 0; o < kMOut; ++o) {
+            const float out = ((acc[o][0] + acc[o][1]) + (acc[o][2] + acc[o][3])) + S.b3[o];
+            const float d = valid ? out - Y[idx * kMOut + o] : 0.f;
+            loss = fmaf(d, d, loss);
+            dout[o] = d * invB;
+        }
+        if (valid) {
+            M.dout[s * kMOut] = dout[0];
+            M.dout[s * kMOut + 1] = dout[1];
+#pragma unroll
+            for (int i = 0; i < kMIn; ++i) M.xs[s * kMIn + i] = x[i];
+        }
+        // dz2 = (dout W3) gelu'(z2): the dz2 record and bf16(dz2) as the next A operand
+#pragma unroll 1
+        for (int cb = 0; cb < kMHid / 16; ++cb) {
+            float d[16];
+            tc_ld16(trow + (uint32_t)(cb * 16), d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float4 w = S.l3[cb * 16 + i];
+                const float dh = fmaf(w.z, dout[1], w.y * dout[0]);
+                d[i] = dh * gelu_d(d[i] + w.x);
+            }
+            if (valid) {
+                float4* dst = reinterpret_cast<float4*>(M.dz2 + s * kMHid + cb * 16);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) dst[v] = make_float4(d[4 * v], d[4 * v + 1], d[4 * v + 2], d[4 * v + 3]);
+            }
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf)
+                *reinterpret_cast<uint4*>(S.A + tc_kmajor_offset(t, cb * 16 + hf * 8)) =
+                    make_uint4(pack_bf16(d[8 * hf], d[8 * hf + 1]), pack_bf16(d[8 * hf + 2], d[8 * hf + 3]),
+                               pack_bf16(d[8 * hf + 4], d[8 * hf + 5]), pack_bf16(d[8 * hf + 6], d[8 * hf + 7]));
+        }
+        if (!tc_block_mma(taddr, a_base, smem_u32(S.Bt), idesc, false, mbar, parity, S.fail)) break;
+        // dz1 = dh1 gelu'(z1), z1 recomputed as in layer 1
+#pragma unroll 1
+        for (int cb = 0; cb < kMHid / 16; ++cb) {
+            float d[16];
+            tc_ld16(trow + (uint32_t)(cb * 16), d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float4 wa = S.l1[cb * 16 + i][0], wb = S.l1[cb * 16 + i][1];
+                float z = wb.y;
+                z = fmaf(wa.x, x[0], z);
+                z = fmaf(wa.y, x[1], z);
+                z = fmaf(wa.z, x[2], z);
+                z = fmaf(wa.w, x[3], z);
+                z = fmaf(wb.x, x[4], z);
+                d[i] = d[i] * gelu_d(z);
+            }
+            if (valid) {
+                float4* dst = reinterpret_cast<float4*>(M.dz1 + s * kMHid + cb * 16);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) dst[v] = make_float4(d[4 * v], d[4 * v + 1], d[4 * v + 2], d[4 * v + 3]);
+            }
+        }
+    }
+    // loss partial of this block (fixed reduction order)
+#pragma unroll
+    for (int dd = 16; dd >= 1; dd >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, dd);
+    if (lane == 0) S.loss[warp] = loss;
+    if (t == 0 && S.fail) atomicExch(M.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+        float sum = 0.f;
+        for (int i = 0; i < kTcThreads / 32; ++i) sum += S.loss[i];
+        M.loss_part[blockIdx.x] = 0.5f * sum * invB;
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+    }
+}
+
+// Weight gradients of a batch: block b sums samples [b chunk, (b+1) chunk)
+// into grad_part[b].  dW2[j][k] = sum_s bf16(dz2[s][j]) h1b[s][k] on the
+// tensor cores with the samples as the reduction dimension: per staged tile
+// of 64 samples, A = bf16(dz2)^T (rows 0..63 of a 128-row tile; rows 64..127
+// stay zero and their accumulator lanes are not read), B = h1b^T (N = k),
+// accumulated in tensor memory over the block's tiles.  The small gradients
+// (W1, b1, b2, W3, b3) on the CUDA cores, one column per thread.
+struct TcGradSmem {
+    alignas(1024) unsigned char A[kTcThreads * kWgTile * 2];  // bf16(dz2)^T, K-major (K = samples)
+    alignas(1024) unsigned char Bh[kMHid * kWgTile * 2];      // h1b^T, K-major
+    unsigned long long mbar;
+    unsigned int taddr;
+    int fail;
+};
+
+__global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(MlpDev M, long long B, long long chunk) {
+    __shared__ TcGradSmem S;
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int i = t; i < (int)(sizeof(S.A) / 16); i += kTcThreads) reinterpret_cast<uint4*>(S.A)[i] = make_uint4(0, 0, 0, 0);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.taddr)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = S.taddr, idesc = tc_idesc_bf16_f32(kTcThreads, kMHid);
+    const uint32_t a_base = smem_u32(S.A), b_base = smem_u32(S.Bh), mbar = smem_u32(&S.mbar);
+    const long long s_begin = (long long)blockIdx.x * chunk;
+    const long long s_end = s_begin + chunk < B ? s_begin + chunk : B;
+    uint32_t parity = 0;
+    bool any = false;
+    for (long long s0 = s_begin; s0 < s_end; s0 += kWgTile) {
+        // thread t stages sample s = t / 2, units [32 (t % 2), 32 (t % 2) + 32)
+        const int sl = t >> 1, j0 = (t & 1) * 32;
+        const long long ss = s0 + sl;
+        const bool ok = ss < s_end;
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+            const int j = j0 + jj;
+            const __nv_bfloat16 a = __float2bfloat16_rn(ok ? M.dz2[ss * kMHid + j] : 0.f);
+            const __nv_bfloat16 b = ok ? M.h1b[ss * kMHid + j] : __float2bfloat16_rn(0.f);
+            *reinterpret_cast<__nv_bfloat16*>(S.A + tc_kmajor_offset(j, sl)) = a;
+            *reinterpret_cast<__nv_bfloat16*>(S.Bh + tc_kmajor_offset(j, sl)) = b;
+        }
+        if (!tc_block_mma(taddr, a_base, b_base, idesc, any, mbar, parity, S.fail)) break;
+        any = true;
+    }
+    float* part = M.grad_part + (size_t)blockIdx.x * kMParams;
+    if (warp < 2) {  // accumulator lanes 0..63: rows j of dW2
+        const int j = t;
+#pragma unroll 1
+        for (int cb = 0; cb < kMHid / 16; ++cb) {
+            float d[16];
+            tc_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) part[oW2 + j * kMHid + cb * 16 + i] = any && !S.fail ? d[i] : 0.f;
+        }
+    }
+    if (t < kMHid) {
+        const int j = t;
+        float gw[kMIn] = {0.f, 0.f, 0.f, 0.f, 0.f}, gb1 = 0.f, gb2 = 0.f;
+        for (long long s = s_begin; s < s_end; ++s) {
+            const float d1 = M.dz1[s * kMHid + j];
+#pragma unroll
+            for (int i = 0; i < kMIn; ++i) gw[i] = fmaf(d1, M.xs[s * kMIn + i], gw[i]);
+            gb1 += d1;
+            gb2 += M.dz2[s * kMHid + j];
+        }
+#pragma unroll
+        for (int i = 0; i < kMIn; ++i) part[oW1 + j * kMIn + i] = gw[i];
+        part[ob1 + j] = gb1;
+        part[ob2 + j] = gb2;
+    } else {
+        const int j = t - kMHid;
+        float g0 = 0.f, g1 = 0.f, d0 = 0.f, d1 = 0.f;
+        for (long long s = s_begin; s < s_end; ++s) {
+            const float h = __bfloat162float(M.h2b[s * kMHid + j]);
+            const float o0 = M.dout[s * kMOut], o1 = M.dout[s * kMOut + 1];
+            g0 = fmaf(o0, h, g0);
+            g1 = fmaf(o1, h, g1);
+            d0 += o0;
+            d1 += o1;
+        }
+        part[oW3 + j] = g0;
+        part[oW3 + kMHid + j] = g1;
+        if (j == 0) {
+            part[ob3] = d0;
+            part[ob3 + 1] = d1;
+        }
+    }
+    if (t == 0 && S.fail) atomicExch(M.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+    }
+}
+
 __global__ void k_psi_nodes(const double* __restrict__ E, int n_cells, double hr, double* __restrict__ psi,
                             float* __restrict__ tab_f) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -834,6 +884,7 @@ struct pic_mlp {
     long long t = 0;  // Adam steps taken
     std::vector<void*> allocs;
     float* loss_host = nullptr;  // pinned
+    int train_per_sm = 1;        // resident blocks of k_mlp_train_tc per SM
 };
 
 namespace {
@@ -860,25 +911,20 @@ void mlp_free(pic_mlp* m) {
     m->loss_host = nullptr;
 }
 
-int fb_grid(const pic_mlp* m, long long B) {
-    const long long tiles = (B + 15) / 16;
-    long long g = (tiles + 3) / 4;
-    const long long cap = (long long)m->sm_count * 8;
-    return (int)(g < 1 ? 1 : (g < cap ? g : cap));
-}
-
 // Forward + backward + weight gradients + reduction (+ Adam when apply).
 cudaError_t mlp_step(pic_mlp* m, long long B, const float* X, const float* Y, long long first, long long mul,
                      long long n_data, int apply, const pic_adam_t* opt) {
     pic::MlpDev& D = m->D;
-    const int gf = fb_grid(m, B);
-    pic::k_mlp_fwd_bwd<<<gf, pic::kFbThreads, 0, m->st>>>(D, X, Y, nullptr, B, first, mul, n_data, 1.0f / (float)B);
+    const long long tiles = (B + pic::kTcThreads - 1) / pic::kTcThreads;
+    const long long cap = (long long)m->sm_count * m->train_per_sm;
+    const int gf = (int)(tiles < cap ? tiles : cap);
+    pic::k_mlp_train_tc<<<gf, pic::kTcThreads, 0, m->st>>>(D, X, Y, B, first, mul, n_data, 1.0f / (float)B);
     long long nwg = (B + pic::kWgTile - 1) / pic::kWgTile;
     if (nwg > pic::kWgMaxBlocks) nwg = pic::kWgMaxBlocks;
     long long chunk = (B + nwg - 1) / nwg;
     chunk = (chunk + pic::kWgTile - 1) / pic::kWgTile * pic::kWgTile;
     nwg = (B + chunk - 1) / chunk;
-    pic::k_mlp_wgrad<<<(int)nwg, pic::kWgThreads, 0, m->st>>>(D, B, chunk);
+    pic::k_mlp_wgrad_tc<<<(int)nwg, pic::kTcThreads, 0, m->st>>>(D, B, chunk);
     pic::AdamArgs A;
     std::memset(&A, 0, sizeof(A));
     if (apply) {
@@ -977,6 +1023,11 @@ int pic_mlp_create(int64_t max_batch, void* stream, pic_mlp** out) {
         pic::k_mlp_refresh<<<(pic::kMParams + 255) / 256, 256, 0, m->st>>>(D);
         e = cudaGetLastError();
     }
+    for (const void* fn : {(const void*)pic::k_mlp_train_tc, (const void*)pic::k_mlp_wgrad_tc})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) m->train_per_sm = pic::tc_blocks_per_sm((const void*)pic::k_mlp_train_tc, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
     if (e != cudaSuccess) {
         mlp_free(m);
@@ -1029,7 +1080,8 @@ int pic_mlp_gradients(pic_mlp* m, int64_t n, const float* X_dev, const float* T_
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad, m->D.grad, sizeof(float) * pic::kMParams, k, m->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, m->D.loss, sizeof(float), k, m->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
-    return mlp_map(e);
+    if (e != cudaSuccess) return mlp_map(e);
+    return pic::mlp_take_error(m, m->st);
 }
 
 int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T_dev, int64_t batch, int64_t steps,
@@ -1057,7 +1109,8 @@ int pic_mlp_train(pic_mlp* m, int64_t n_data, const float* X_dev, const float* T
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
-    return mlp_map(e);
+    if (e != cudaSuccess) return mlp_map(e);
+    return pic::mlp_take_error(m, m->st);
 }
 
 int pic_mlp_apply_gradient(pic_mlp* m, const float* grad, int ptr_kind, const pic_adam_t* opt) {
