@@ -94,24 +94,31 @@ __device__ __forceinline__ void flush32(const DevParams& P, const WinBufs32& B, 
 }
 
 // Field tables of one cycle from its global charge: exact int64 trapezoid
-// sums S_j = g_j - g_c, then in FP64 E_j = S_j q_unit/2 * (1/r_j) and
-// E_c = Q_c q_unit / h_r, rounded once to binary32 together with the
-// differences E_{j+1} - E_j.  q is the int64 scan input (2 Np1), g the scan
-// output, reused for E in FP64.
+// sums S_j = g_j - g_c, then in binary32 E_j = float(S_j) cq_j with the
+// per-node constant cq_j = q_unit / (2 r_j) (negated left of the axis for
+// the odd reading) and E_c = float(Q_c) cq_c, cq_c = q_unit / h_r (0 for the
+// odd reading); the table holds (E_j, E_{j+1} - E_j).  Each E_j is within
+// 1.5 units in the last place of the exact node field, which the binary32
+// bound of the form covers with a wide margin (a field error dE moves a
+// particle by about h dE per stage).  All on the FP32 pipes: on this GPU the
+// FP64 conversion of every node in every block was most of the build.  q is
+// the int64 scan input (2 Np1), g the scan output, reused for E.
 // stop_src (may be null): the not-done count of the cycle, read together with
 // the charge; *s_stop = (count == 0) after the call.
 __device__ void build_fields32(const DevParams& P, const unsigned long long* Qg, long long* q, long long* g,
-                               float2* tab, const double* inv_r, float* edges, long long* s_warp, long long* s_c,
+                               float2* tab, const float* cq, float* edges, long long* s_warp, long long* s_c,
                                const int* stop_src = nullptr, int* s_stop = nullptr) {
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
+    const float qh = (float)P.q_half;
     if (stop_src && threadIdx.x == 0) *s_stop = (__ldcg(stop_src) == 0);
-    auto emit = [&](int f, int j, double e, double en, long long S) {
-        tab[f * Np1 + j] = make_float2((float)e, j < Nc ? (float)(en - e) : 0.0f);
+    auto field_at = [&](int j, long long S, long long qj) -> float { return __ll2float_rn(j == c ? qj : S) * cq[j]; };
+    auto emit = [&](int f, int j, float e, float en, long long S) {
+        tab[f * Np1 + j] = make_float2(e, j < Nc ? en - e : 0.0f);
         // odd reading: the lower edge value carries the sign flip (rE / |R|)
-        if (j == 0) edges[2 * f] = (float)(P.parity_odd ? -(i64_to_double(S) * P.q_half) : i64_to_double(S) * P.q_half);
-        if (j == Nc) edges[2 * f + 1] = (float)(i64_to_double(S) * P.q_half);
+        if (j == 0) edges[2 * f] = P.parity_odd ? -(__ll2float_rn(S) * qh) : __ll2float_rn(S) * qh;
+        if (j == Nc) edges[2 * f + 1] = __ll2float_rn(S) * qh;
     };
-    if (field_build_regs(P, Qg, inv_r, s_warp, emit)) {
+    if (field_build_regs_with(P, Qg, s_warp, field_at, emit)) {
         __syncthreads();
         return;
     }
@@ -124,22 +131,18 @@ __device__ void build_fields32(const DevParams& P, const unsigned long long* Qg,
         s_c[2 + threadIdx.x] = q[threadIdx.x * Np1 + c];
     }
     __syncthreads();
-    double* e = (double*)g;
+    float* e = (float*)g;  // E_idx in the slot of g[idx] (float 2 idx), which only this thread reads
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int f = idx >= Np1, j = idx - f * Np1;
-        const double Sd = i64_to_double(g[idx] - s_c[f]);
-        double ev;
-        if (j == c) ev = P.parity_odd ? 0.0 : (i64_to_double(s_c[2 + f]) * P.q_unit) * P.inv_hr;
-        else ev = (Sd * P.q_half) * inv_r[j];
-        if (P.parity_odd && j < c) ev = -ev;
-        if (j == 0) edges[2 * f] = (float)(P.parity_odd ? -(Sd * P.q_half) : Sd * P.q_half);
-        if (j == Nc) edges[2 * f + 1] = (float)(Sd * P.q_half);
-        e[idx] = ev;
+        const long long S = g[idx] - s_c[f];
+        if (j == 0) edges[2 * f] = P.parity_odd ? -(__ll2float_rn(S) * qh) : __ll2float_rn(S) * qh;
+        if (j == Nc) edges[2 * f + 1] = __ll2float_rn(S) * qh;
+        e[2 * idx] = field_at(j, S, s_c[2 + f]);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < 2 * Np1; idx += blockDim.x) {
         const int j = idx >= Np1 ? idx - Np1 : idx;
-        tab[idx] = make_float2((float)e[idx], j < Nc ? (float)(e[idx + 1] - e[idx]) : 0.0f);
+        tab[idx] = make_float2(e[2 * idx], j < Nc ? e[2 * idx + 2] - e[2 * idx] : 0.0f);
     }
     __syncthreads();
 }
@@ -292,15 +295,16 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
     const int copies = P.hist_copies;
     unsigned int* hist = (unsigned int*)smem_raw;  // copies x 2 fields x hw words
     long long* g = (long long*)(hist + copies * 2 * hw);  // 2 Np1
-    double* inv_r = (double*)(g + 2 * Np1);         // Np1
-    float2* tabA = (float2*)(inv_r + Np1);          // 2 Np1: fields of R1, R3
+    float* cq = (float*)(g + 2 * Np1);              // Np1 (in a slot of Np1 doubles)
+    float2* tabA = (float2*)((double*)(g + 2 * Np1) + Np1);  // 2 Np1: fields of R1, R3
     float2* tabB = tabA + 2 * Np1;                  // 2 Np1: fields of R2, R4
     __shared__ float s_edA[4], s_edB[4];
     __shared__ long long s_warp[64], s_c[4];
     __shared__ int s_ok, s_cnt, s_stop, s_next;
 
     for (int j = threadIdx.x; j < Np1; j += blockDim.x)
-        inv_r[j] = (j == P.c) ? 0.0 : 1.0 / (P.r_min + (double)j * P.hr);
+        cq[j] = (j == P.c) ? (P.parity_odd ? 0.0f : (float)(P.q_unit * P.inv_hr))
+                           : (float)(((P.parity_odd && j < P.c) ? -P.q_half : P.q_half) / (P.r_min + (double)j * P.hr));
 
     const bool detect_only = mode == MODE_PERIODS, fine_only = mode == MODE_FINE;
     const long long n = P.n, ld = B.ld;
@@ -434,7 +438,7 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
         if (lb == 0 && threadIdx.x == 0) B.notdone[(k + 1) % 3] = 0;
         if (threadIdx.x == 0 && s_cnt) atomicAdd(&B.notdone[k % 3], s_cnt);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok, (unsigned int)nb)) return;
-        build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabA, inv_r, s_edA,
+        build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabA, cq, s_edA,
                        s_warp, s_c, track ? &B.notdone[k % 3] : nullptr, &s_stop);
         if (track && s_stop) {
             K = k;
@@ -478,7 +482,7 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
         __syncthreads();
         flush32(P, B, hist, cyc, lb);
         if (!grid_sync(P, B.bar, gen, B.status, &s_ok, (unsigned int)nb)) return;
-        build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabB, inv_r, s_edB,
+        build_fields32(P, B.Qring + (size_t)(cyc % 3) * 2 * Np1 * kQPad, (long long*)hist, g, tabB, cq, s_edB,
                        s_warp, s_c);
         ++cyc;
     }

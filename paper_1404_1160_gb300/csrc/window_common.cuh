@@ -68,16 +68,16 @@ static __device__ void block_exscan_pairs2(const long long* q, long long* g, int
 // first nodes of the next warp, so that every lane finds E_{j+1} of its
 // last node in the next lane.  q_j comes from the cycle's global charge Qg;
 // the exact trapezoid sums g_j = sum_{m<j} (q_m + q_{m+1}) are a warp scan
-// plus the totals of the preceding warps (s_tot), S_j = g_j - g_c, and
-//   E_j = (S_j q_unit/2) (1/r_j),  E_c = (q_c q_unit) (1/h_r),
-// the same operations in the same order as the staged build (with the odd
-// reading, E_j = -E_j left of the axis and E_c = 0).  Each owned
-// node is passed to emit(f, j, E_j, E_{j+1}, S_j) (E_{j+1} unused at
-// j = n_cells).  Covers n_cells + 1 <= 31 R (blockDim/64) nodes; returns
-// false (doing nothing) when R = 4 would not suffice.  s_tot: 64 int64.
-template <int R, class Emit>
+// plus the totals of the preceding warps (s_tot), S_j = g_j - g_c, and the
+// node field is field_at(j, S_j, q_j) (binary64 or binary32: its type is
+// the table's).  Each owned node is passed to emit(f, j, E_j, E_{j+1}, S_j)
+// (E_{j+1} unused at j = n_cells).  Covers n_cells + 1 <= 31 R (blockDim/64)
+// nodes; returns false (doing nothing) when R = 4 would not suffice.
+// s_tot: 64 int64.
+template <int R, class FieldAt, class Emit>
 static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, const unsigned long long* Qg,
-                                                          const double* inv_r, long long* s_tot, Emit emit) {
+                                                          long long* s_tot, FieldAt field_at, Emit emit) {
+    using Val = decltype(field_at(0, 0ll, 0ll));
     const int Nc = P.n_cells, Np1 = Nc + 1, c = P.c;
     const int H = blockDim.x >> 1;
     const int f = threadIdx.x >= H ? 1 : 0;
@@ -110,23 +110,18 @@ static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, co
     }
     __syncthreads();
     const long long gc = s_tot[f * 32 + 16];
-    auto field_at = [&](int j, long long S, long long qj) -> double {
-        if (j > Nc) return 0.0;
-        if (j == c) return P.parity_odd ? 0.0 : (i64_to_double(qj) * P.q_unit) * P.inv_hr;
-        const double e = (i64_to_double(S) * P.q_half) * inv_r[j];
-        return (P.parity_odd && j < c) ? -e : e;  // odd reading: rE / |r|
-    };
+    auto value = [&](int j, long long S, long long qj) -> Val { return j > Nc ? Val(0) : field_at(j, S, qj); };
     long long S = g0 - gc;
-    double Ecur = field_at(j0, S, q[0]);
-    const double En = __shfl_down_sync(0xffffffffu, Ecur, 1);
+    Val Ecur = value(j0, S, q[0]);
+    const Val En = __shfl_down_sync(0xffffffffu, Ecur, 1);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int j = j0 + r;
         long long Sn = S;
-        double Enext = En;
+        Val Enext = En;
         if (r + 1 < R) {
             Sn = S + ((j < Nc) ? q[r] + q[(r + 1) % R] : 0ll);
-            Enext = field_at(j + 1, Sn, q[(r + 1) % R]);
+            Enext = value(j + 1, Sn, q[(r + 1) % R]);
         }
         if (lane != 31 && j <= Nc) emit(f, j, Ecur, Enext, S);
         Ecur = Enext;
@@ -134,18 +129,34 @@ static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, co
     }
 }
 
-template <class Emit>
-static __device__ __forceinline__ bool field_build_regs(const DevParams& P, const unsigned long long* Qg,
-                                                        const double* inv_r, long long* s_tot, Emit emit) {
+template <class FieldAt, class Emit>
+static __device__ __forceinline__ bool field_build_regs_with(const DevParams& P, const unsigned long long* Qg,
+                                                             long long* s_tot, FieldAt field_at, Emit emit) {
     const int per_pass = 31 * (int)(blockDim.x >> 6);  // nodes covered per node of a thread
     const int Np1 = P.n_cells + 1;
     if ((blockDim.x & 63) != 0 || blockDim.x > 1024) return false;
-    if (Np1 <= per_pass) field_build_regs_r<1>(P, Qg, inv_r, s_tot, emit);
-    else if (Np1 <= 2 * per_pass) field_build_regs_r<2>(P, Qg, inv_r, s_tot, emit);
-    else if (Np1 <= 3 * per_pass) field_build_regs_r<3>(P, Qg, inv_r, s_tot, emit);
-    else if (Np1 <= 4 * per_pass) field_build_regs_r<4>(P, Qg, inv_r, s_tot, emit);
+    if (Np1 <= per_pass) field_build_regs_r<1>(P, Qg, s_tot, field_at, emit);
+    else if (Np1 <= 2 * per_pass) field_build_regs_r<2>(P, Qg, s_tot, field_at, emit);
+    else if (Np1 <= 3 * per_pass) field_build_regs_r<3>(P, Qg, s_tot, field_at, emit);
+    else if (Np1 <= 4 * per_pass) field_build_regs_r<4>(P, Qg, s_tot, field_at, emit);
     else return false;
     return true;
+}
+
+// The binary64 field of the FP64 path:
+//   E_j = (S_j q_unit/2) (1/r_j),  E_c = (q_c q_unit) (1/h_r),
+// the same operations in the same order as the staged build (with the odd
+// reading, E_j = -E_j left of the axis and E_c = 0).
+template <class Emit>
+static __device__ __forceinline__ bool field_build_regs(const DevParams& P, const unsigned long long* Qg,
+                                                        const double* inv_r, long long* s_tot, Emit emit) {
+    const int c = P.c;
+    auto field_at = [&](int j, long long S, long long qj) -> double {
+        if (j == c) return P.parity_odd ? 0.0 : (i64_to_double(qj) * P.q_unit) * P.inv_hr;
+        const double e = (i64_to_double(S) * P.q_half) * inv_r[j];
+        return (P.parity_odd && j < c) ? -e : e;  // odd reading: rE / |r|
+    };
+    return field_build_regs_with(P, Qg, s_tot, field_at, emit);
 }
 
 // Barrier of the n_blocks blocks that share `bar` (the whole grid, or the
