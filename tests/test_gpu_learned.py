@@ -306,14 +306,17 @@ def test_learned_step_constant_correction_matches_oracle_on_poisson(parity, sort
     m.close()
 
 
-def test_learned_step_network_matches_oracle_on_poisson():
+# 300_007 particles: two or three 128-particle tiles per block of the
+# tensor-core correction kernel
+@pytest.mark.parametrize("n", [20_001, 300_007])
+def test_learned_step_network_matches_oracle_on_poisson(n):
     # a non-trivial network (random weights, nonzero biases): the oracle gives
     # an interval for each binary32 network output (oracle.mlp's interval
     # form); the decision is compared wherever it is the same over the whole
     # interval, and a kept state must lie in the corrected interval
     p = pic.pic_default_params(dt=0.4, r_min=-2.0, r_max=2.0)
     c = cfg_of(p)
-    R0, V0 = inputs.gaussian_beam(20_001, seed=22)
+    R0, V0 = inputs.gaussian_beam(n, seed=22)
     w = inputs.mlp_init(23)
     rng = np.random.default_rng(24)
     pp = omlp.unflatten(w.astype(np.float64))

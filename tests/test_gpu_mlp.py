@@ -55,7 +55,9 @@ def weights(seed, scale=1.0):
     return (omlp.flatten(p) * scale).astype(np.float32)
 
 
-@pytest.mark.parametrize("n", [1, 17, 4096, 100_003])
+# 400_003 samples: several 128-sample tiles per block of the tensor-core kernel
+# (its mbarrier phase, A buffer and accumulator reused from tile to tile)
+@pytest.mark.parametrize("n", [1, 17, 4096, 100_003, 400_003])
 def test_forward_matches_oracle(n):
     m = pic.pic_mlp_create(16)
     w = weights(1)
@@ -73,7 +75,9 @@ def test_forward_matches_oracle(n):
     m.close()
 
 
-@pytest.mark.parametrize("n", [16, 1000, 8192])
+# 150_000 samples: two tiles for some blocks of the per-sample kernel and ten
+# 64-sample tiles accumulated in tensor memory per weight-gradient block
+@pytest.mark.parametrize("n", [16, 1000, 8192, 150_000])
 def test_gradients_match_oracle(n):
     m = pic.pic_mlp_create(n)
     w = weights(3)
