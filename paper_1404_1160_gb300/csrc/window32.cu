@@ -17,9 +17,9 @@
 // Field cycle (Poisson): as in the FP64 kernel, stages pair up (1,3) and
 // (2,4); each pair is deposited by one sweep into per-block 32-bit
 // histograms, flushed with 64-bit global atomics, and after a grid barrier
-// every block turns the global int64 charge into its own field table.  The
-// conversion S -> E runs in FP64 (the only FP64 arithmetic of the form) and
-// the table holds binary32 (E_j, E_{j+1} - E_j).  Two tables are kept: the
+// every block turns the global int64 charge into its own field table of
+// binary32 (E_j, E_{j+1} - E_j), computed in binary32 from the exact int64
+// sums and per-node constants (build_fields32).  Two tables are kept: the
 // one of pair 1 (fields of R1, R3) and the one of pair 2 (R2, R4), so the
 // first sweep of the next step can recompute e1 and e3 instead of reading
 // them back from memory.
