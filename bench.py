@@ -381,6 +381,9 @@ def measure(wl_name, n, steps, warmup, rank=0, world=1, with_e2e=True, with_erro
                    "l2": "L2 flushed between timed steps (256 MB write); per-step trajectory store > L2"},
         "roofline": roofline,
         "gpu_launches": int(launches),
+        # FP64 windows that replayed with every trajectory row (the stored
+        # band around the forecast landing rows missed one), warm-up included
+        "band_replays": int(mom["band_replays"]),
         "wall_s": wall,
         "clocks": clocks,
         "error_vs_oracle": ("FP32 form: see error_vs_fp64 (binary32 bounds checked against the FP64 oracle in the "

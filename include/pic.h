@@ -177,6 +177,12 @@ typedef struct {
     double  window_ms;         /* device time of the window kernel launches of
                                   the last pic_step call (CUDA events)         */
     int64_t window_launches;   /* window kernel launches of that call           */
+    int64_t band_replays;      /* FP64 Poisson ETD windows since pic_init that
+                                  replayed with every trajectory row: the
+                                  window stores only the rows around the
+                                  landing rows forecast from the previous
+                                  step's periods, and a landing row outside
+                                  them makes it run again (same results)    */
 } pic_moments_t;
 
 /* Diagnostics of the current state (computed by device reductions; one small

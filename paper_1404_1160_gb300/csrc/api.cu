@@ -234,6 +234,8 @@ struct pic_handle {
     double t = 0.0;
     long long n_steps = 0;
     int have_periods = 0;
+    int band_skip = 0;         // ETD windows left to run with every trajectory row (after a band miss)
+    long long band_replays = 0;
     long long launches = 0;
     // CUDA events around the window launches of the last pic_step call
     std::vector<cudaEvent_t> ev;
@@ -246,6 +248,16 @@ struct pic_handle {
     int64_t acc_n = 0;
     int64_t acc_fine = 0;
 };
+
+namespace {
+
+// Trajectory band of the FP64 ETD window: rows within kBandMargin of the
+// predicted landing rows; after a replay the next kBandSkip windows store
+// every row.
+constexpr int kBandMargin = 1;
+constexpr int kBandSkip = 8;
+
+}  // namespace
 
 namespace {
 
@@ -281,7 +293,7 @@ int read_status(pic_handle* h) {
 cudaError_t reset_coop(pic_handle* h) {
     const size_t Np1 = (size_t)h->dp.n_cells + 1;
     cudaError_t e = cudaMemsetAsync(h->B.Qring, 0, sizeof(unsigned long long) * 3 * 2 * Np1 * pic::kQPad, h->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.notdone, 0, sizeof(int) * 3, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->B.notdone, 0, sizeof(int) * 4, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.bar, 0, sizeof(unsigned int) * 64, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->B.K_out, 0, sizeof(long long), h->st);
     return e;
@@ -327,6 +339,7 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     if (e != cudaSuccess) return map_cuda(e);
     const int T_known = (mode == pic::MODE_ETD && h->prm.periods_once) ? 1 : 0;
     h->ev_used = 0;
+    bool banded = false;
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         const long long reps = mode == pic::MODE_ETD ? n_iter : 1;
         for (long long s = 0; s < reps && e == cudaSuccess; ++s) {
@@ -334,12 +347,25 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
             if (e == cudaSuccess) e = reset_coop(h);
             const bool timed = e == cudaSuccess && ensure_events(h, h->ev_used + 2) == cudaSuccess;
             if (timed) cudaEventRecord(h->ev[h->ev_used], h->st);
+            // FP64 ETD windows store only the trajectory rows around the
+            // landing rows predicted from the previous step's periods
+            pic::DevParams dp = h->dp;
+            dp.band_m = 0;
+            if (mode == pic::MODE_ETD && !T_known && !h->prec && (h->have_periods || s > 0) &&
+                h->prm.max_window_steps + 3 + 2 * kBandMargin < 4096) {
+                if (h->band_skip > 0) {
+                    --h->band_skip;
+                } else {
+                    dp.band_m = kBandMargin;
+                    banded = true;
+                }
+            }
             if (e == cudaSuccess) {
                 const long long nf = mode == pic::MODE_FINE ? n_iter : 0;
                 if (h->prec)
-                    e = pic::launch_window32_coop(h->dp, h->B32, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin32);
+                    e = pic::launch_window32_coop(dp, h->B32, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin32);
                 else
-                    e = pic::launch_window_coop(h->dp, h->B, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin);
+                    e = pic::launch_window_coop(dp, h->B, h->L, mode, T_known, nf, h->st, &h->launches, h->Tin);
             }
             if (timed) {
                 cudaEventRecord(h->ev[h->ev_used + 1], h->st);
@@ -361,6 +387,16 @@ int run_window(pic_handle* h, int mode, long long n_iter) {
     }
     if (e != cudaSuccess) return map_cuda(e);
     const int rc = read_status(h);
+    if (!rc && banded) {
+        // a window whose landing rows fell outside the stored band replayed
+        // itself with every row; after one, the next windows store every row
+        int replays = 0;
+        e = cudaMemcpyAsync(&replays, h->B.notdone + 4, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (replays > h->band_replays) h->band_skip = kBandSkip;
+        h->band_replays = replays;
+    }
     collect_window_ms(h);
     if (h->acc_on && mode == pic::MODE_FINE) h->acc_fine += n_iter;
     return rc;
@@ -427,7 +463,7 @@ int init32(pic_handle* h, const double* r0, const double* v0, int ptr_kind) {
     }
     if (need_traj) ALLOC(B.traj, (size_t)p->max_window_steps * LD);
     if (p->periods_once) ALLOC(h->Tin32, N);
-    ALLOC(h->B.notdone, 3);
+    ALLOC(h->B.notdone, 5);
     ALLOC(h->B.bar, 64);
     ALLOC(h->B.status, 1);
     ALLOC(h->B.K_out, 1);
@@ -583,6 +619,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     } while (0)
     ALLOC(B.y, N);
     ALLOC(B.t1, N);
+    ALLOC(B.vp, N);
     ALLOC(B.T, N);
     ALLOC(B.o, N);
     ALLOC(B.N, N);
@@ -614,7 +651,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
     }
     if (need_traj) ALLOC(B.traj, ((size_t)p->max_window_steps + 1) * N);
     if (p->periods_once) ALLOC(h->Tin, N);
-    ALLOC(B.notdone, 3);
+    ALLOC(B.notdone, 5);
     ALLOC(B.bar, 64);
     ALLOC(B.status, 1);
     ALLOC(B.K_out, 1);
@@ -650,6 +687,7 @@ int pic_init(const pic_params* p, int64_t n, const double* r0, const double* v0,
         if (e == cudaSuccess) e = cudaMemsetAsync(B.tr, 0, sizeof(int2) * N, h->st);
         rc = map_cuda(e);
     }
+    if (!rc) rc = map_cuda(cudaMemsetAsync(B.notdone, 0, sizeof(int) * 5, h->st));
     if (!rc) {
         pic::SortBufs& S = h->sort;
         S.y = &h->B.y;
@@ -957,6 +995,7 @@ int pic_moments(pic_handle* h, pic_moments_t* out) {
     }
     out->window_ms = h->window_ms;
     out->window_launches = h->window_n;
+    out->band_replays = h->band_replays;
     if (h->prm.field_model == PIC_FIELD_POISSON) {
         std::vector<int64_t> Q((size_t)h->dp.n_cells + 1);
         int64_t nout = 0;

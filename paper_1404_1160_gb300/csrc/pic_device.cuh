@@ -41,6 +41,9 @@ struct DevParams {
     int xs_fma;                        // 1 when inv_hr is a power of two
     LocFixed loc;                      // the same locate on the integer pipe (xs_fma meshes)
     int imul;                          // 1: products by the rotation constants on the integer pipe
+    int band_m;                        // > 0: an ETD window stores only the trajectory rows within band_m of
+                                       // the landing rows predicted from the previous period (a miss
+                                       // replays the window with every row); 0: every row
     // algorithm
     int field, solver;                 // PIC_FIELD_*, PIC_FINE_*
     int Kmax;                          // window cap (fine steps)

@@ -47,6 +47,7 @@ cudaError_t launch_gather(const DevParams& P, const double* R, long long n, cons
 struct WinBufs {
     double2* y;                 // current fine sample (R, V)
     double *t1, *T, *o;         // first extremum, period, remainder (fine steps)
+    double* vp;                 // V_{k-1} of a sign change found at sample k (its root is taken at k+1)
     int* N;                     // whole periods per macro step
     int2* tr;                   // (Track flags, last sample needed)
     double2* ce;                // values carried across a field cycle (fields / partial sums)
@@ -56,7 +57,7 @@ struct WinBufs {
     double* cxr;                // Lawson: (Phi_h y)_R
     double2* traj;              // (Kmax+1) rows of n samples (R, V)
     unsigned long long* Qring;  // 3 cycles x 2 fields x (n_cells+1), one node per kQPad words
-    int* notdone;               // 3 cycles
+    int* notdone;               // 3 cycles; [3] trajectory band missed (this launch); [4] band replays
     unsigned int* bar;          // grid barrier: [0] arrivals, [32] released generation
     int* status;                // DEV_* of the launch
     long long* K_out;           // fine steps of the window

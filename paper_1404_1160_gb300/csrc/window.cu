@@ -139,8 +139,8 @@ __device__ void build_fields(const DevParams& P, const unsigned long long* Qg, l
 
 // Period tracking of one particle at sample k (k >= 1), V_{k-1} = Vold,
 // V_k = Vnew.  A sign change between samples k-1 and k is marked pending
-// and its root taken at sample k+1 from V_{k-1}, V_k, V_{k+1} (V_{k-1} read
-// back from the trajectory store): the same crossings, stencils and order as
+// and its root taken at sample k+1 from V_{k-1}, V_k, V_{k+1} (V_{k-1} kept
+// in vp when the change is found): the same crossings, stencils and order as
 // testing samples k-2, k-1 at sample k.  tr = (flags, need) is loaded by the
 // caller and updated here.  Returns true when the particle is done.
 __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& B, long long i, int k,
@@ -152,7 +152,7 @@ __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& 
         s.need = tr.y;
         bool touched = false;
         if (s.flags & F_PEND) {
-            const double v0 = B.traj[(size_t)(k - 2) * P.n + i].y;
+            const double v0 = B.vp[i];
             if ((s.flags & F_NEXT) >= 1) s.t1 = B.t1[i];
             s.flags &= ~F_PEND;
             track_root(s, P, k, v0, Vold, Vnew, detect_only);
@@ -161,6 +161,7 @@ __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& 
         }
         if (!(s.flags & F_RES) && positive(Vold) != positive(Vnew)) {
             s.flags |= F_PEND;
+            B.vp[i] = Vold;
             touched = true;
         }
         if (k == P.Kmax) {
@@ -181,6 +182,25 @@ __device__ __forceinline__ bool track_update(const DevParams& P, const WinBufs& 
     }
     if (!(tr.x & F_RES)) return false;
     return detect_only || k >= tr.y;
+}
+
+// Trajectory band of an ETD window.  The landing reads rows floor(o) .. +2
+// and floor(o + T) .. +2; with the previous step's period as the forecast
+// of T, a window stores row 0 (y^n) and the rows within band_m of the two
+// forecast stencils only.  The first rows of the two bands sit in bits
+// 8..19 and 20..31 of the tracking word (the flags use bits 0..4).
+__device__ __forceinline__ int band_bits(const DevParams& P, double Tprev) {
+    const double T = (Tprev > 0.0 && isfinite(Tprev)) ? Tprev : P.Tfb;
+    const double o = fmod(P.D, T);
+    const int N = (int)rint((P.D - o) / T);
+    int a = (int)floor(o) - P.band_m, b = N > 0 ? (int)floor(o + T) - P.band_m : a;
+    a = min(max(a, 0), 4095);
+    b = min(max(b, 0), 4095);
+    return (int)(((unsigned int)a << 8) | ((unsigned int)b << 20));
+}
+__device__ __forceinline__ bool band_holds(int x, int k, int band_m) {
+    const unsigned int ux = (unsigned int)x, L = 3u + 2u * (unsigned int)band_m;
+    return k == 0 || (unsigned int)(k - (int)((ux >> 8) & 0xFFFu)) < L || (unsigned int)(k - (int)(ux >> 20)) < L;
 }
 
 // ------------------------------------------------ cooperative Poisson window
@@ -313,7 +333,13 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     unsigned int gen = 0;
     int cyc = 0;
     int K = 0;
+    __shared__ int s_miss;
+    const bool band_ok = mode == MODE_ETD && !T_known && P.band_m > 0;
 
+    // attempt 1 replays the window with every trajectory row when a landing
+    // row fell outside the band of attempt 0
+    for (int attempt = 0;; ++attempt) {
+    const bool band = band_ok && attempt == 0;
     if (!fine_only) {
         for (long long i = i0; i < n; i += stride) {
             if (T_known) {
@@ -326,7 +352,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                 B.N[i] = s.N;
                 B.tr[i] = make_int2(s.flags, s.need);
             } else {
-                B.tr[i] = make_int2(0, 0);
+                B.tr[i] = make_int2(band ? band_bits(P, B.T[i]) : 0, 0);
             }
         }
     }
@@ -390,7 +416,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
                     int2 tr = in.tr;
                     // the sample is stored before tracking: a pending root at
                     // sample k+1 reads it back
-                    if (!((tr.x & F_RES) && (detect_only || k > tr.y)))
+                    if (!((tr.x & F_RES) && (detect_only || k > tr.y)) && (!band || band_holds(tr.x, k, P.band_m)))
                         __stcs(&B.traj[(size_t)k * n + i], make_double2(Rn, Vn));
                     const bool done = track_update(P, B, i, k, V, Vn, detect_only, tr);
                     cnt += done ? 0u : 1u;
@@ -524,12 +550,27 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     }
     if (mode != MODE_ETD) return;
 
-    // ---- landing (step 3) and extrapolation (step 4)
+    // ---- landing (step 3) and extrapolation (step 4); with the band, a
+    // particle whose landing rows were not all stored marks a miss
+    bool miss = false;
     for (long long i = i0; i < n; i += stride) {
         const double o = B.o[i], T = B.T[i];
         const int N = B.N[i];
-        double y[2][2];
         const int nt = N > 0 ? 2 : 1;
+        if (band) {
+            const int x = B.tr[i].x;
+            bool held = true;
+            for (int t = 0; t < nt; ++t) {
+                const int kk = (int)floor(t == 0 ? o : o + T);
+                held = held && band_holds(x, kk, P.band_m) && band_holds(x, kk + 1, P.band_m) &&
+                       band_holds(x, kk + 2, P.band_m);
+            }
+            if (!held) {
+                miss = true;
+                continue;
+            }
+        }
+        double y[2][2];
         for (int t = 0; t < nt; ++t) {
             const double u = t == 0 ? o : o + T;
             const int kk = (int)floor(u);
@@ -541,6 +582,23 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
             y[t][1] = interp3(a.y, b.y, cc.y, sf);
         }
         B.y[i] = make_double2(extrapolate(y[0][0], y[nt - 1][0], N), extrapolate(y[0][1], y[nt - 1][1], N));
+    }
+    if (!band) return;
+    if (__syncthreads_or(miss) && threadIdx.x == 0) atomicOr(&B.notdone[3], 1);
+    if (!grid_sync(P, B.bar, gen, B.status, &s_ok, gridDim.x)) return;
+    if (threadIdx.x == 0) s_miss = ld_acquire_s32(&B.notdone[3]);
+    __syncthreads();
+    if (!s_miss) return;
+    // replay from y^n (row 0) with every row, for every particle; the charge
+    // buffer of the next cycle is the clear one
+    for (long long i = i0; i < n; i += stride) B.y[i] = B.traj[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B.notdone[0] = B.notdone[1] = B.notdone[2] = 0;
+        atomicAdd(&B.notdone[4], 1);
+    }
+    ++cyc;
+    K = 0;
+    if (!grid_sync(P, B.bar, gen, B.status, &s_ok, gridDim.x)) return;
     }
 }
 

@@ -95,6 +95,7 @@ class pic_moments_t(C.Structure):
         ("n_no_period", C.c_int64),
         ("window_ms", C.c_double),
         ("window_launches", C.c_int64),
+        ("band_replays", C.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -71,7 +71,7 @@ def test_struct_layout_matches_header(lib):
 
     # pic_params: 2 doubles, 4 int32, 3 doubles, uint64, 6 int32, int64, 2 int32
     assert ctypes.sizeof(pic.pic_params) == 2 * 8 + 4 * 4 + 3 * 8 + 8 + 6 * 4 + 8 + 2 * 4
-    assert ctypes.sizeof(pic.pic_moments_t) == 21 * 8
+    assert ctypes.sizeof(pic.pic_moments_t) == 22 * 8
 
 
 def test_bad_arguments_rejected_without_device(lib):

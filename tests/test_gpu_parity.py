@@ -362,6 +362,41 @@ def test_checkpoint_resume_is_bit_identical():
     pic.pic_destroy(c)
 
 
+def test_trajectory_band_miss_replays_the_window_bit_identically():
+    # the FP64 ETD window stores only the trajectory rows around the landing
+    # rows forecast from the previous step's periods; wrong periods in a
+    # restored state make the forecast miss, the window replays with every
+    # row, and the step equals the one forecast from the true periods
+    p = pic.pic_default_params()
+    R0, V0 = inputs.gaussian_beam(20_000, seed=31, r_cut=4.0)
+    a = pic.pic_init(p, R0, V0)
+    b = pic.pic_init(p, R0, V0)
+    pic.pic_step(a, 2)
+    pic.pic_step(b, 2)
+    st = pic.pic_get_state(b)
+    st["T"] = st["T"] * 0.6
+    pic.pic_set_state(b, st)
+    pic.pic_step(a, 1)
+    pic.pic_step(b, 1)
+    Ra, Va = pic.pic_get_particles(a)
+    Rb, Vb = pic.pic_get_particles(b)
+    assert bit_equal(Ra, Rb) and bit_equal(Va, Vb)
+    ma, mb = pic.pic_moments(a), pic.pic_moments(b)
+    assert ma["band_replays"] == 0 and mb["band_replays"] == 1
+    Ta, Na, oa = pic.pic_get_periods(a)
+    Tb, Nb, ob = pic.pic_get_periods(b)
+    assert bit_equal(Ta, Tb) and np.array_equal(Na, Nb) and bit_equal(oa, ob)
+    # the windows after a replay store every row for a while: still the same
+    pic.pic_step(a, 3)
+    pic.pic_step(b, 3)
+    Ra, Va = pic.pic_get_particles(a)
+    Rb, Vb = pic.pic_get_particles(b)
+    assert bit_equal(Ra, Rb) and bit_equal(Va, Vb)
+    assert pic.pic_moments(a)["band_replays"] == 0 and pic.pic_moments(b)["band_replays"] == 1
+    pic.pic_destroy(a)
+    pic.pic_destroy(b)
+
+
 def test_empty_run():
     p = pic.pic_default_params()
     h = pic.pic_init(p, np.zeros(0), np.zeros(0))
