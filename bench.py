@@ -374,6 +374,7 @@ def measure(wl_name, n, steps, warmup, rank=0, world=1, with_e2e=True, with_erro
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step_min_median_max": [float(np.min(step_ms)), float(np.median(step_ms)), float(np.max(step_ms))],
         "dtype": "f32" if f32 else "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"], "n_particles": n, "fine_steps_per_window": K, "dt": prm.dt,
@@ -407,7 +408,8 @@ def form_summary(line, ref_value=None, ref_dt=None):
     """The keys of a form entry: its throughput, timing, roofline, clocks and
     errors; with the FP64 headline's value, the speed-up per macro step and
     per unit of simulated time."""
-    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "clocks",
+    keep = ("value", "unit", "ms_per_step", "ms_per_step_min_median_max", "steps", "warmup", "dtype", "config",
+            "roofline", "clocks", "band_replays",
             "gpu_launches", "error_vs_fp64", "learned", "error_vs_oracle")
     out = {k: line[k] for k in keep if k in line}
     if ref_value:

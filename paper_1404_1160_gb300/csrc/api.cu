@@ -811,11 +811,10 @@ int pic_step_learned(pic_handle* h, const pic_mlp* m, int64_t n_steps, float sca
     }
     if (rc) return rc;
     if (e != cudaSuccess) return map_cuda(e);
-    if ((rc = pic::mlp_take_error(m, h->st))) return rc;
     unsigned long long nfb = 0;
     e = cudaMemcpyAsync(&nfb, h->n_fb, sizeof(nfb), cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return map_cuda(e);
+    if ((rc = pic::mlp_take_error(m, h->st))) return rc;  // synchronises the stream: nfb has arrived
     if (n_fallback) *n_fallback = (int64_t)nfb;
     return PIC_OK;
 }
