@@ -542,6 +542,17 @@ def measure_batch(wl_name, steps, warmup, with_e2e=True):
     value = n_total * steps / dev_s
     launches = pic.pic_batch_launch_count(b) - launches0
     Ks = np.array([pic.pic_batch_moments(b, i)["window_steps"] for i in range(len(beams))])
+    # each beam's own window time in the shared launch (device timer), averaged
+    # over three more steps: which beams set the step
+    beam_ms = np.zeros(len(beams))
+    for _ in range(3):
+        pic.pic_batch_step(b, 1)
+        beam_ms += np.array([pic.pic_batch_moments(b, i)["window_ms"] for i in range(len(beams))]) / 3.0
+    slow = int(np.argmax(beam_ms))
+    beam_window = {"max": float(beam_ms.max()), "median": float(np.median(beam_ms)), "min": float(beam_ms.min()),
+                   "slowest_beam": {"n_particles": int(sizes[slow]), "eps": float(params[slow].eps),
+                                    "n_cells": int(params[slow].n_cells), "field_model": int(params[slow].field_model),
+                                    "fine_steps_per_window": int(Ks[slow])}}
     e2e = None
     if with_e2e:
         # end to end with host buffers: every beam's (R, V) in and out each step
@@ -573,6 +584,7 @@ def measure_batch(wl_name, steps, warmup, with_e2e=True):
         "config": {"workload": wl["desc"], "n_beams": len(beams), "n_particles_total": n_total,
                    "n_particles_min": int(sizes.min()), "n_particles_max": int(sizes.max()), "dt": wl["batch"]["dt"],
                    "fine_steps_per_window_max": int(Ks.max()), "tuned": tuned, "tune_s": t_tune,
+                   "beam_window_ms": beam_window,
                    "parallelism": "single GPU", "l2": "L2 flushed between timed steps (256 MB write)"},
         "roofline": {"bound": "hbm", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,

@@ -385,6 +385,9 @@ typedef struct {
     int32_t graph_error;               /* cudaError_t of a failed capture, else 0   */
     int32_t hist_copies;               /* copies of each block's charge histogram   */
     double  alloc_power;
+    int32_t shares_measured;           /* 1: block shares from the beams' measured
+                                          window times (pic_batch_tune), 0: in
+                                          proportion to N_p^alloc_power        */
 } pic_batch_config_t;
 
 int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n_particles,
@@ -401,11 +404,17 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
 /* Autotuner: times steps_per_trial macro steps (after one warm step) for
    each launch shape (block size x blocks per SM x allocation power x
    histogram copies) that fits, keeps the fastest, then times the sort
-   periods 1, 4, 16 and keeps the fastest.  The trial steps are real steps of the batch (their results
-   do not depend on the shape).  *best receives the chosen configuration. */
+   periods 1, 4, 16 and keeps the fastest.  Then it sets the block shares
+   from the beams' measured window times (each beam's time x blocks, as
+   its work) while that makes the step at least 1 % faster.  The trial
+   steps are real steps of the batch (their results do not depend on the
+   shape or the shares).  *best receives the chosen configuration. */
 int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind);
 int pic_batch_set_particles(pic_batch* b, int32_t beam, const double* r, const double* v, int ptr_kind);
+/* Moments of one beam.  Its window_ms is the beam's own part of the last
+   batch step's launch (from the first of its blocks starting to the last
+   finishing, on the device's global timer), window_launches 1. */
 int pic_batch_moments(pic_batch* b, int32_t beam, pic_moments_t* out);
 int64_t pic_batch_steps(const pic_batch* b);
 int64_t pic_batch_launch_count(const pic_batch* b);

@@ -1,4 +1,5 @@
 // api.cu -- host side of the C ABI declared in include/pic.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1297,9 +1298,12 @@ struct pic_batch {
     pic::BeamDesc32* d_desc = nullptr;
     int* d_status = nullptr;
     int* h_status = nullptr;  // pinned
+    unsigned long long* d_times = nullptr;  // per beam: first start, last end of its blocks (ns)
+    unsigned long long* h_times = nullptr;  // pinned copy
     std::vector<pic::BeamDesc32> desc;
     int block = 1024, bps = 1, grid = 0, sort_every = 4, copies = 1;
     double alloc_power = 1.0;
+    bool shares_measured = false;  // block shares from measured beam times (pic_batch_tune)
     size_t smem = 0;
     int max_cells = 0;
     cudaGraphExec_t exec = nullptr;
@@ -1332,6 +1336,7 @@ cudaError_t batch_upload(pic_batch* b) {
         d.Tin = h->prm.periods_once ? h->Tin32 : nullptr;
         d.T_known = h->prm.periods_once ? 1 : 0;
         d.coop = h->prm.field_model == PIC_FIELD_POISSON ? 1 : 0;
+        d.t_ns = b->d_times + 2 * i;
     }
     batch_drop_graph(b);
     return cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(pic::BeamDesc32) * b->n, cudaMemcpyHostToDevice, b->st);
@@ -1339,8 +1344,8 @@ cudaError_t batch_upload(pic_batch* b) {
 
 // Blocks per beam in proportion to (its particles)^power, at least one and
 // at most what its particles fill; weight 1/4 for the analytic fields (no
-// field cycle).
-int batch_configure(pic_batch* b, int block, int bps_want, double power, int copies) {
+// field cycle).  wts (may be null): the beams' weights instead.
+int batch_configure(pic_batch* b, int block, int bps_want, double power, int copies, const double* wts = nullptr) {
     if (block < 128 || block > 1024 || (block & 31)) return PIC_ERR_INVALID_ARG;
     if (copies != 1 && copies != 2 && copies != 4) return PIC_ERR_INVALID_ARG;
     const size_t smem = pic::window32_batch_smem(b->max_cells, copies);
@@ -1367,7 +1372,7 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power, int cop
         const long long groups = (h->B32.ld + 127) / 128;
         need[i] = coop ? (groups + block / 32 - 1) / (block / 32) : (h->n + block - 1) / block;
         if (need[i] < 1) need[i] = 1;
-        w[i] = (coop ? 1.0 : 0.25) * std::pow((double)(h->n > 0 ? h->n : 1), power);
+        w[i] = wts ? wts[i] : (coop ? 1.0 : 0.25) * std::pow((double)(h->n > 0 ? h->n : 1), power);
         wsum += w[i];
     }
     long long used = 0;
@@ -1407,6 +1412,7 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power, int cop
     b->block = block;
     b->bps = bps;
     b->alloc_power = power;
+    b->shares_measured = wts != nullptr;
     b->copies = copies;
     b->smem = smem;
     return map_cuda(batch_upload(b));
@@ -1417,6 +1423,8 @@ cudaError_t batch_enqueue_step(pic_batch* b, cudaStream_t st) {
     if (e == cudaSuccess) e = pic::launch_window32_batch(b->d_desc, b->n, b->grid, b->block, b->smem, st);
     if (e == cudaSuccess) e = pic::launch_batch_status(b->d_desc, b->n, b->d_status, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_times, b->d_times, sizeof(unsigned long long) * 2 * b->n, cudaMemcpyDeviceToHost, st);
     return e;
 }
 
@@ -1465,10 +1473,15 @@ int batch_one_step(pic_batch* b) {
     b->launches += 3;
     for (int i = 0; i < b->n; ++i)
         if (b->h_status[i] != pic::DEV_OK) return map_dev(b->h_status[i]);
-    for (pic_handle* h : b->hs) {
+    for (int i = 0; i < b->n; ++i) {
+        pic_handle* h = b->hs[i];
         h->t += h->prm.dt;
         h->n_steps += 1;
         h->have_periods = 1;
+        // the beam's window within the shared launch: first start to last end of its blocks
+        const unsigned long long t0 = b->h_times[2 * i], t1 = b->h_times[2 * i + 1];
+        h->window_ms = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+        h->window_n = 1;
     }
     b->steps += 1;
     return PIC_OK;
@@ -1486,6 +1499,8 @@ void batch_free(pic_batch* b) {
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_status) cudaFree(b->d_status);
     if (b->h_status) cudaFreeHost(b->h_status);
+    if (b->d_times) cudaFree(b->d_times);
+    if (b->h_times) cudaFreeHost(b->h_times);
     delete b;
 }
 
@@ -1526,6 +1541,8 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
         cudaError_t e = cudaMalloc(&b->d_desc, sizeof(pic::BeamDesc32) * n_beams);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int) * n_beams);
         if (e == cudaSuccess) e = cudaMallocHost(&b->h_status, sizeof(int) * n_beams);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_times, sizeof(unsigned long long) * 2 * n_beams);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->h_times, sizeof(unsigned long long) * 2 * n_beams);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gst, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
         rc = map_cuda(e);
@@ -1567,6 +1584,7 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out) {
     out->graph = b->use_graph ? 1 : 0;
     out->graph_error = (int32_t)b->graph_error;
     out->hist_copies = b->copies;
+    out->shares_measured = b->shares_measured ? 1 : 0;
     return PIC_OK;
 }
 
@@ -1586,11 +1604,16 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
         }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIC_ERR_CUDA;
+    std::vector<double> beam_ms(b->n);  // each beam's mean window time over the last trial
     auto trial = [&](double* ms) -> int {
         int rc = batch_one_step(b);  // capture and warm
         if (rc) return rc;
+        std::fill(beam_ms.begin(), beam_ms.end(), 0.0);
         cudaEventRecord(e0, b->st);
-        for (int s = 0; s < steps_per_trial && !rc; ++s) rc = batch_one_step(b);
+        for (int s = 0; s < steps_per_trial && !rc; ++s) {
+            rc = batch_one_step(b);
+            for (int i = 0; i < b->n; ++i) beam_ms[i] += b->hs[i]->window_ms / steps_per_trial;
+        }
         cudaEventRecord(e1, b->st);
         cudaEventSynchronize(e1);
         float x = 0.f;
@@ -1630,6 +1653,29 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
             }
         }
         b->sort_every = best_sort;
+    }
+    // Block shares from measured beam times: a beam whose window took t_i on
+    // n_i blocks did about t_i n_i block-time of work; shares in proportion
+    // to that, within the same limits, even the windows out.  Repeated while
+    // the step gets at least 1 % faster; the shares that timed best stay.
+    if (!rc) {
+        double cur_ms = 0.0;
+        rc = trial(&cur_ms);
+        std::vector<double> cur_w;  // empty: the power-law shares
+        for (int it = 0; it < 4 && !rc; ++it) {
+            std::vector<double> w(b->n);
+            for (int i = 0; i < b->n; ++i) w[i] = std::max(beam_ms[i], 1e-6) * (double)b->desc[i].n_blocks;
+            const int r = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies, w.data());
+            if (r == PIC_ERR_UNSUPPORTED) break;
+            if ((rc = r)) break;
+            double ms = 0.0;
+            if ((rc = trial(&ms))) break;
+            if (!(ms < 0.99 * cur_ms)) break;
+            cur_ms = ms;
+            cur_w = w;
+        }
+        if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies,
+                                      cur_w.empty() ? nullptr : cur_w.data());
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

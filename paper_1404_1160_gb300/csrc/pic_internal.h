@@ -125,6 +125,7 @@ struct BeamDesc32 {
     int first_block, n_blocks;
     int coop;             // 1: Poisson (cooperative window), 0: analytic field (per particle)
     int T_known;
+    unsigned long long* t_ns;  // [2]: first start and last end (global timer, ns) of the beam's blocks
 };
 size_t window32_batch_smem(int max_cells, int copies);
 cudaError_t window32_batch_attr(size_t smem);

@@ -755,9 +755,12 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_batch(const BeamDes
     }
     __syncthreads();
     const int lb = (int)blockIdx.x - D.first_block;
+    if (threadIdx.x == 0) atomicMin(&D.t_ns[0], (unsigned long long)global_ns());
     if (D.coop) window32_coop_body(D.P, D.B, MODE_ETD, D.T_known, 0, D.Tin, lb, D.n_blocks, smem_raw);
     else if (D.P.field == 1) window32_local_body<1>(D.P, D.B, MODE_ETD, D.T_known, 1, D.Tin, lb, D.n_blocks);
     else window32_local_body<2>(D.P, D.B, MODE_ETD, D.T_known, 1, D.Tin, lb, D.n_blocks);
+    __syncthreads();  // the block's last thread is done before its end time
+    if (threadIdx.x == 0) atomicMax(&D.t_ns[1], (unsigned long long)global_ns());
 }
 
 __global__ void k_batch_reset(const BeamDesc32* __restrict__ beams, int n_beams) {
@@ -773,6 +776,8 @@ __global__ void k_batch_reset(const BeamDesc32* __restrict__ beams, int n_beams)
     if (threadIdx.x == 0) {
         *D.B.K_out = 0;
         *D.B.status = 0;
+        D.t_ns[0] = ~0ull;
+        D.t_ns[1] = 0ull;
     }
 }
 

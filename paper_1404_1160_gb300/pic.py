@@ -45,7 +45,8 @@ class pic_adam_t(C.Structure):
 
 class pic_batch_config_t(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("grid", C.c_int32), ("sort_every", C.c_int32),
-                ("graph", C.c_int32), ("graph_error", C.c_int32), ("hist_copies", C.c_int32), ("alloc_power", C.c_double)]
+                ("graph", C.c_int32), ("graph_error", C.c_int32), ("hist_copies", C.c_int32), ("alloc_power", C.c_double),
+                ("shares_measured", C.c_int32)]
 
 
 class pic_params(C.Structure):
@@ -517,7 +518,8 @@ def pic_batch_set_config(b: Batch, block: int, blocks_per_sm: int, alloc_power: 
 
 def _cfg_dict(c) -> dict:
     return {"block": c.block, "blocks_per_sm": c.blocks_per_sm, "grid": c.grid, "sort_every": c.sort_every,
-            "graph": c.graph, "graph_error": c.graph_error, "hist_copies": c.hist_copies, "alloc_power": c.alloc_power}
+            "graph": c.graph, "graph_error": c.graph_error, "hist_copies": c.hist_copies, "alloc_power": c.alloc_power,
+            "shares_measured": c.shares_measured}
 
 
 def pic_batch_get_config(b: Batch) -> dict:
