@@ -406,7 +406,8 @@ int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
    histogram copies) that fits, keeps the fastest, then times the sort
    periods 1, 4, 16 and keeps the fastest.  Then it sets the block shares
    from the beams' measured window times (each beam's time x blocks, as
-   its work) while that makes the step at least 1 % faster.  The trial
+   its work) while that makes the step at least 0.5 % faster (at most 8
+   rounds).  The trial
    steps are real steps of the batch (their results do not depend on the
    shape or the shares).  *best receives the chosen configuration. */
 int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);

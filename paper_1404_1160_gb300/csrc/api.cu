@@ -1657,12 +1657,12 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
     // Block shares from measured beam times: a beam whose window took t_i on
     // n_i blocks did about t_i n_i block-time of work; shares in proportion
     // to that, within the same limits, even the windows out.  Repeated while
-    // the step gets at least 1 % faster; the shares that timed best stay.
+    // the step gets at least 0.5 % faster; the shares that timed best stay.
     if (!rc) {
         double cur_ms = 0.0;
         rc = trial(&cur_ms);
         std::vector<double> cur_w;  // empty: the power-law shares
-        for (int it = 0; it < 4 && !rc; ++it) {
+        for (int it = 0; it < 8 && !rc; ++it) {
             std::vector<double> w(b->n);
             for (int i = 0; i < b->n; ++i) w[i] = std::max(beam_ms[i], 1e-6) * (double)b->desc[i].n_blocks;
             const int r = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies, w.data());
@@ -1670,7 +1670,7 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
             if ((rc = r)) break;
             double ms = 0.0;
             if ((rc = trial(&ms))) break;
-            if (!(ms < 0.99 * cur_ms)) break;
+            if (!(ms < 0.995 * cur_ms)) break;
             cur_ms = ms;
             cur_w = w;
         }

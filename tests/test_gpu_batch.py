@@ -93,7 +93,7 @@ def test_batch_equals_single_beams_and_ignores_the_launch_shape():
 
 def test_autotuner_steps_are_real_steps():
     beams = make_beams()
-    ref = single_runs(beams, 1 + 15 * 3 + 3 * 3 + 5 * 3 + 2)
+    ref = single_runs(beams, 1 + 15 * 3 + 3 * 3 + 9 * 3 + 2)
     b = pic.pic_batch_create([make_params(sp) for sp in SPECS], beams)
     pic.pic_batch_step(b, 1)
     best = pic.pic_batch_tune(b, steps_per_trial=2)
@@ -108,9 +108,9 @@ def test_autotuner_steps_are_real_steps():
 
 
 def ref_steps(done):
-    # the reference above ran 1 + (up to 15 shapes + 3 sort periods + up to 5
+    # the reference above ran 1 + (up to 15 shapes + 3 sort periods + up to 9
     # trials of measured block shares) x 3 + 2 steps
-    return 1 + 15 * 3 + 3 * 3 + 5 * 3 + 2 - done
+    return 1 + 15 * 3 + 3 * 3 + 9 * 3 + 2 - done
 
 
 def test_batch_rejects_the_fp64_path():
