@@ -86,9 +86,10 @@ typedef struct {
                                   (the Duffing case of Sec. 4.1); 0: every step  */
     int32_t  precision;        /* 0 = FP64; 1 = FP32 form: particle state and push
                                   in binary32 (Lawson RK4 in the rotating frame,
-                                  compensated integer+fraction times), FP64 only
-                                  in the charge -> field conversion and in
-                                  pic_moments; needs PIC_FINE_LAWSON_RK4, W <=
+                                  compensated integer+fraction times, the field
+                                  table from the exact int64 charge in
+                                  binary32), FP64 only in pic_moments; needs
+                                  PIC_FINE_LAWSON_RK4, W <=
                                   2^32 (Poisson) and dt/h < 2^22, else
                                   PIC_ERR_UNSUPPORTED                            */
     int32_t  block_size;       /* CUDA threads per block, 0 = library default

@@ -30,12 +30,16 @@ constexpr int kHistCopiesMax = 2;
 // Shared-memory histogram of one field.  HIST = 0: three 32-bit counters
 // per cell (particles C_j, low and high 16 bits of the right weights S_j),
 // exact while a block deposits at most 65536 positions per field per cycle;
-// the node charge is Q_j = W C_j - S_j + S_{j-1}.  HIST = 1: one 64-bit
-// counter per node.
+// the node charge is Q_j = W C_j - S_j + S_{j-1}.  HIST = 2: four counters
+// (C_j and the 11/11/10-bit parts of S_j), exact up to 2^21 positions per
+// block, field and cycle, for the larger particle counts.  HIST = 1: one
+// 64-bit counter per node (W > 2^32, or beyond 2^21 positions).
 template <int HIST>
 struct Hist {
-    static constexpr int kWordsPerNode = HIST == 0 ? 3 : 2;  // 32-bit words per node
+    static constexpr int kWordsPerNode = HIST == 0 ? 3 : (HIST == 2 ? 4 : 2);  // 32-bit words per node
 };
+// 32-bit words per node that the shared-memory layout reserves
+__host__ __device__ constexpr int hist_slot_words(int hist) { return hist == 2 ? 4 : 3; }
 
 template <int HIST>
 __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cell& c, long long W) {
@@ -47,6 +51,13 @@ __device__ __forceinline__ void deposit_cell(unsigned int* h, int Np1, const Cel
         atomicAdd(&h[c.j], 1u);
         if (lo) atomicAdd(&h[Np1 + c.j], lo);
         if (hi) atomicAdd(&h[2 * Np1 + c.j], hi);
+    } else if (HIST == 2) {
+        const unsigned int q = (unsigned int)c.qR;
+        const unsigned int a = q & 0x7ffu, b = (q >> 11) & 0x7ffu, d = q >> 22;
+        atomicAdd(&h[c.j], 1u);
+        if (a) atomicAdd(&h[Np1 + c.j], a);
+        if (b) atomicAdd(&h[2 * Np1 + c.j], b);
+        if (d) atomicAdd(&h[3 * Np1 + c.j], d);
     } else {
         unsigned long long* h64 = (unsigned long long*)h;
         atomicAdd(&h64[c.j], (unsigned long long)(W - c.qR));
@@ -70,6 +81,21 @@ __device__ __forceinline__ unsigned long long hist_node(const unsigned int* h, i
                 Sj += ((unsigned long long)hc[2 * Np1 + j] << 16) + (unsigned long long)hc[Np1 + j];
             }
             if (j >= 1) Sm += ((unsigned long long)hc[2 * Np1 + j - 1] << 16) + (unsigned long long)hc[Np1 + j - 1];
+        }
+        return C * (unsigned long long)W - Sj + Sm;
+    } else if (HIST == 2) {
+        auto S = [&](const unsigned int* hc, int m) -> unsigned long long {
+            return (unsigned long long)hc[Np1 + m] + ((unsigned long long)hc[2 * Np1 + m] << 11) +
+                   ((unsigned long long)hc[3 * Np1 + m] << 22);
+        };
+        unsigned long long C = 0, Sj = 0, Sm = 0;
+        for (int c = 0; c < copies; ++c) {
+            const unsigned int* hc = h + c * stride;
+            if (j < Np1 - 1) {
+                C += hc[j];
+                Sj += S(hc, j);
+            }
+            if (j >= 1) Sm += S(hc, j - 1);
         }
         return C * (unsigned long long)W - Sj + Sm;
     } else {
@@ -294,7 +320,7 @@ __global__ void __launch_bounds__(kWinMaxThreads) k_window_coop(DevParams P, Win
     Stage* stage = (Stage*)smem_raw;                      // STAGE: 2 per warp
     double2* tab = (double2*)(smem_raw + (STAGE ? (blockDim.x >> 5) * kStageBytesPerWarp : 0));  // 2 Np1
     unsigned int* hist = (unsigned int*)(tab + 2 * Np1);  // copies x 2 fields x words (also the scan input)
-    long long* g = (long long*)(hist + (copies > 2 ? copies : 2) * 2 * 3 * Np1);  // 2 Np1
+    long long* g = (long long*)(hist + (copies > 2 ? copies : 2) * 2 * hist_slot_words(HIST) * Np1);  // 2 Np1
     double* inv_r = (double*)(g + 2 * Np1);               // Np1
     __shared__ double s_edges[4];
     __shared__ long long s_warp[64];
@@ -795,11 +821,12 @@ __global__ void k_moments(DevParams P, WinBufs B, double* part_d, long long* par
 // Shared memory of the window kernel with `copies` histogram copies (at
 // least two copies' worth: the histogram region doubles as the int64 scan
 // input) and, with staging, two Stage buffers per warp.
-static size_t coop_smem_bytes(int n_cells, int copies, int block, int stage) {
+static size_t coop_smem_bytes(int n_cells, int copies, int block, int stage, int slot_words) {
     const size_t Np1 = (size_t)n_cells + 1;
     const size_t hc = (size_t)(copies > 2 ? copies : 2);
     return (stage ? (size_t)(block / 32) * kStageBytesPerWarp : 0) + 2 * Np1 * sizeof(double2) +
-           hc * 2 * 3 * Np1 * sizeof(unsigned int) + 2 * Np1 * sizeof(long long) + Np1 * sizeof(double);
+           hc * 2 * (size_t)slot_words * Np1 * sizeof(unsigned int) + 2 * Np1 * sizeof(long long) +
+           Np1 * sizeof(double);
 }
 
 template <int SOLVER, int HIST, int POW2>
@@ -807,13 +834,15 @@ static void* coop_fn3(int stage) {
     return stage ? (void*)k_window_coop<SOLVER, HIST, POW2, 1> : (void*)k_window_coop<SOLVER, HIST, POW2, 0>;
 }
 
+template <int SOLVER, int POW2>
+static void* coop_fn2(int hist, int stage) {
+    return hist == 0 ? coop_fn3<SOLVER, 0, POW2>(stage)
+                     : (hist == 2 ? coop_fn3<SOLVER, 2, POW2>(stage) : coop_fn3<SOLVER, 1, POW2>(stage));
+}
+
 static void* coop_fn(int solver, int hist, int pow2, int stage) {
-    if (pow2) {
-        if (solver == 1) return hist == 0 ? coop_fn3<1, 0, 1>(stage) : coop_fn3<1, 1, 1>(stage);
-        return hist == 0 ? coop_fn3<0, 0, 1>(stage) : coop_fn3<0, 1, 1>(stage);
-    }
-    if (solver == 1) return hist == 0 ? coop_fn3<1, 0, 0>(stage) : coop_fn3<1, 1, 0>(stage);
-    return hist == 0 ? coop_fn3<0, 0, 0>(stage) : coop_fn3<0, 1, 0>(stage);
+    if (pow2) return solver == 1 ? coop_fn2<1, 1>(hist, stage) : coop_fn2<0, 1>(hist, stage);
+    return solver == 1 ? coop_fn2<1, 0>(hist, stage) : coop_fn2<0, 0>(hist, stage);
 }
 
 cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_count, WindowLaunch* L) {
@@ -821,15 +850,19 @@ cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_co
     // staging when the block's shared memory stays within the per-block
     // limit; then as many histogram copies (up to kHistCopiesMax) as fit
     const size_t limit = 220 * 1024;
-    L->stage = coop_smem_bytes(P.n_cells, 1, block, 1) <= limit ? 1 : 0;
-    int copies = kHistCopiesMax;
-    while (copies > 1 && coop_smem_bytes(P.n_cells, copies, block, L->stage) > limit) copies >>= 1;
-    P.hist_copies = copies;
-    L->coop_smem = coop_smem_bytes(P.n_cells, copies, block, L->stage);
-    // positions one block deposits into one field per cycle
+    // positions one block deposits into one field per cycle: at most the
+    // chunks of 32 of one block, with at least one block per SM
+    const long long n_chunks = (P.n + 31) / 32;
     long long need_blocks = (P.n + block - 1) / block;
+    const long long min_grid = need_blocks < sm_count ? (need_blocks < 1 ? 1 : need_blocks) : sm_count;
+    const int slot = (n_chunks + min_grid - 1) / min_grid * 32 > 65536 ? hist_slot_words(2) : hist_slot_words(0);
+    L->stage = coop_smem_bytes(P.n_cells, 1, block, 1, slot) <= limit ? 1 : 0;
+    int copies = kHistCopiesMax;
+    while (copies > 1 && coop_smem_bytes(P.n_cells, copies, block, L->stage, slot) > limit) copies >>= 1;
+    P.hist_copies = copies;
+    L->coop_smem = coop_smem_bytes(P.n_cells, copies, block, L->stage, slot);
     int bps = 1 << 30;
-    for (int hh = 0; hh < 2; ++hh) {
+    for (int hh = 0; hh < 3; ++hh) {
         void* fn = coop_fn(P.solver, hh, P.xs_fma, L->stage);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->coop_smem);
         if (e != cudaSuccess) return e;
@@ -844,10 +877,14 @@ cudaError_t window_prepare(DevParams& P, int block, int blocks_per_sm, int sm_co
     long long grid = (long long)bps * sm_count;
     if (need_blocks < grid) grid = need_blocks < 1 ? 1 : need_blocks;
     L->coop_grid = (int)grid;
-    // the split 32-bit histogram needs qR < 2^32 (W <= 2^32) and at most
-    // 65536 positions per block, field and cycle
-    const long long per_thread = (P.n + grid * block - 1) / (grid * block);
-    L->hist = (per_thread * block <= 65536 && P.W <= (1ll << 32)) ? 0 : 1;
+    // the split 32-bit histograms need qR < 2^32 (W <= 2^32) and at most
+    // 65536 (HIST 0) or 2^21 (HIST 2, when the layout has its fourth word)
+    // positions per block, field and cycle
+    const long long per_block = (n_chunks + grid - 1) / grid * 32;
+    if (P.W > (1ll << 32)) L->hist = 1;
+    else if (per_block <= 65536) L->hist = 0;
+    else if (slot == hist_slot_words(2) && per_block <= (1ll << 21)) L->hist = 2;
+    else L->hist = 1;
     if (L->hist == 1) P.hist_copies = 1;
     return cudaSuccess;
 }

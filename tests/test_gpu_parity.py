@@ -397,6 +397,25 @@ def test_trajectory_band_miss_replays_the_window_bit_identically():
     pic.pic_destroy(b)
 
 
+def test_beam_beyond_65536_particles_per_block_matches_the_oracle():
+    # more than 65536 positions per block, field and cycle (one block per
+    # SM): the window's charge histogram takes four 32-bit words per node
+    # (count and 11/11/10-bit parts of the weights) instead of three; one
+    # macro step bit for bit against the oracle (20 fine steps per turn keep
+    # the oracle's single-core step short)
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 2048 * 32 * sm + 1003
+    p = pic.pic_default_params(steps_per_turn=20, max_window_steps=80)
+    c = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(n, seed=41, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    pic.pic_step(h, 1)
+    R, V = pic.pic_get_particles(h)
+    ref = oracle.etd_step(c, R0, V0)
+    assert bit_equal(R, ref.R) and bit_equal(V, ref.V)
+    pic.pic_destroy(h)
+
+
 def test_empty_run():
     p = pic.pic_default_params()
     h = pic.pic_init(p, np.zeros(0), np.zeros(0))
