@@ -111,6 +111,7 @@ BYTES_PER_PARTICLE_FINE_STEP_F32 = 16
 # they were taken from
 PROFILES = {
     "vp1e6": ("window_coop_vp1e6.md", ["paper_1404_1160_gb300/csrc/window.cu",
+                                       "paper_1404_1160_gb300/csrc/window_coop.cuh",
                                        "paper_1404_1160_gb300/csrc/window_common.cuh",
                                        "paper_1404_1160_gb300/csrc/pic_device.cuh"]),
     "vp1e8_f32": ("window32_coop_vp1e8_f32.md", ["paper_1404_1160_gb300/csrc/window32.cu",

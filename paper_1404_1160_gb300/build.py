@@ -17,6 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
 SOURCES = ["api.cu", "mesh.cu", "window.cu", "window32.cu", "sort.cu", "mlp.cu"]
+# window_coop.cu compiles once per (histogram form, fine solver): its kernel
+# instantiations build in parallel
+VARIANTS = [("window_coop.cu", f"window_coop_h{h}_s{s}", [f"-DPIC_WINDOW_HIST={h}", f"-DPIC_WINDOW_SOLVER={s}"])
+            for h in (0, 1, 2) for s in (0, 1)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -47,12 +51,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     headers.append(os.path.join(ROOT, "include", "pic.h"))
     objs = []
     jobs = []
-    for src in SOURCES:
+    units = [(src, src.replace(".cu", ""), []) for src in SOURCES] + VARIANTS
+    for src, name, defs in units:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, name + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *_flags(), *(extra or []), "-c", s, "-o", o])
+            jobs.append([nvcc(), *_flags(), *defs, *(extra or []), "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(len(jobs)) as ex:
             res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
