@@ -718,8 +718,8 @@ FALLBACK_HBM_GBS = 6800.0  # one earlier copy-bandwidth measurement on a GB300
 
 
 def measured_hbm_peak():
-    """HBM peak in B/s and where it comes from: the measured copy bandwidth
-    of the GB300s when MEASURED_PEAKS.json is present, else the
+    """HBM peak in B/s and where it comes from: the measured GB300 copy
+    bandwidth in MEASURED_PEAKS.json when the file is present, else the
     fallback figure."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
