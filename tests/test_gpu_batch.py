@@ -176,3 +176,58 @@ def test_every_beam_of_a_mixed_batch_matches_the_oracle():
         assert m["n_steps"] == n_macro
     assert off_mesh > 0
     b.close()
+
+
+@pytest.mark.slow
+def test_full_size_batch64_workload():
+    # The 64-beam workload at full size (1.6e7 particles): with all beams in
+    # one launch, the four smallest beams match the FP64 oracle's two macro
+    # steps within the binary32 bound; after the autotuner (the launch shape
+    # and measured block shares the bench times) they still equal their
+    # single-beam runs bit for bit; every beam keeps its charge exactly and
+    # stays finite throughout
+    import bench
+
+    params, beams = bench.batch_specs(bench.WORKLOADS["batch64"])
+    beams = [(f32(R).astype(np.float64), f32(V).astype(np.float64)) for R, V in beams]
+    sizes = np.array([R.size for R, _ in beams])
+    small = [int(i) for i in np.argsort(sizes)[:4]]
+    b = pic.pic_batch_create(params, beams)
+
+    def check_all(steps):
+        for i, (p, (R0, _)) in enumerate(zip(params, beams)):
+            R, V = pic.pic_batch_get_particles(b, i)
+            assert np.isfinite(R).all() and np.isfinite(V).all(), i
+            m = pic.pic_batch_moments(b, i)
+            assert m["n_steps"] == steps
+            if p.field_model == pic.PIC_FIELD_POISSON:
+                assert m["Q_total"] + m["n_out_of_mesh"] * p.weight_fixed == R0.size * p.weight_fixed, i
+
+    pic.pic_batch_step(b, 2)
+    check_all(2)
+    for i in small:
+        p, (R0, V0) = params[i], beams[i]
+        cfg = cfg_of(p)
+        T = oracle.periods(cfg, R0, V0)[0] if p.periods_once else None
+        Ro, Vo, K, N_max = R0, V0, 0, 0
+        for _ in range(2):
+            res = oracle.etd_step(cfg, Ro, Vo, T)
+            Ro, Vo = res.R, res.V
+            K = max(K, res.stats["window_steps"])
+            N_max = max(N_max, int(res.N.max()))
+        R, V = pic.pic_batch_get_particles(b, i)
+        scale = max(1.0, float(np.max(np.hypot(Ro, Vo))))
+        bound = etd_bound(2, K, N_max, scale)
+        assert max_err(R, Ro) <= bound and max_err(V, Vo) <= bound, (i, sizes[i], bound)
+    cfg_t = pic.pic_batch_tune(b, steps_per_trial=1)
+    pic.pic_batch_step(b, 1)
+    steps = pic.pic_batch_steps(b)
+    check_all(steps)
+    for i in small:
+        h = pic.pic_init(params[i], *beams[i])
+        pic.pic_step(h, steps)
+        Rs, Vs = pic.pic_get_particles(h)
+        pic.pic_destroy(h)
+        R, V = pic.pic_batch_get_particles(b, i)
+        assert bit_equal(R, Rs) and bit_equal(V, Vs), (i, cfg_t)
+    b.close()

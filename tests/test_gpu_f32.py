@@ -337,6 +337,35 @@ def test_histogram_copies_at_scale_within_binary32_bound():
     assert m["Q_total"] + m["n_out_of_mesh"] * p.weight_fixed == n * p.weight_fixed
 
 
+@pytest.mark.slow
+def test_full_size_fp32_workload_charge_is_exact():
+    # The 1e8-particle FP32 workload at full size, in the launch
+    # configuration the bench times (eps 0.001, 1024 cells, window cap 202,
+    # sort every 4 steps): after one macro step the charge the library
+    # deposits from its state equals the oracle's binary32 deposit of that
+    # state bit for bit, the charge is conserved exactly, every particle is
+    # finite and the kinetic energy moves by far less than 1e-3.
+    n = 100_000_000
+    p = pic.pic_default_params(precision=1, eps=1e-3, n_cells=1024, max_window_steps=202, sort_every=4)
+    cfg = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(n, seed=0, r_cut=4.0)
+    h = pic.pic_init(p, R0, V0)
+    del R0, V0
+    m0 = pic.pic_moments(h)
+    pic.pic_step(h, 1)
+    m1 = pic.pic_moments(h)
+    R, V = pic.pic_get_particles(h)
+    assert np.isfinite(R).all() and np.isfinite(V).all()
+    Q, E, edges, n_out = pic.pic_get_field(h, p.n_cells)
+    pic.pic_destroy(h)
+    Qo, no = oracle.deposit_f32(cfg, f32(R))
+    assert np.array_equal(Q, Qo) and n_out == no
+    assert int(Q.sum()) + n_out * p.weight_fixed == n * p.weight_fixed
+    assert m1["Q_total"] + m1["n_out_of_mesh"] * p.weight_fixed == n * p.weight_fixed
+    assert abs(m1["kinetic"] - m0["kinetic"]) < 1e-3 * m0["kinetic"]
+    assert m1["window_steps"] <= 202 and m1["N_min"] >= 14
+
+
 def test_odd_field_reading_within_binary32_bound():
     p = pic.pic_default_params(precision=1, field_parity=pic.PIC_PARITY_ODD)
     cfg = cfg_of(p)

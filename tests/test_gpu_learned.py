@@ -260,17 +260,18 @@ def _constant_net(c_R, c_V):
     return m, w
 
 
-def _oracle_certainty(c, plain, dR_lo, dR_hi, dV_lo, dV_hi, tol, E, edges):
+def _oracle_certainty(c, plain, dR_lo, dR_hi, dV_lo, dV_hi, tol, E, edges, precision=0):
     """Per particle: (certain keep, certain fallback) of the energy check over
     every correction in the box [dR_lo, dR_hi] x [dV_lo, dV_hi], with a
-    margin for the rounding of H on either side (1e-10 of |H| + eps max|psi|)."""
+    margin for the rounding of H on either side (1e-10 of |H| + eps max|psi|);
+    precision 1: the FP32 form's binary32 corrected state."""
     H0 = OL.frozen_energy(c, plain.R, plain.V, E, edges)
     psi_scale = float(np.abs(OL.node_potential(c, E)).max()) if E is not None else 0.0
     amb = 1e-10 * (np.abs(H0) + c.eps * psi_scale + 1e-300)
     ms = []
     for dR in (dR_lo, dR_hi):
         for dV in (dV_lo, dV_hi):
-            ms.append(OL.learned_apply(c, plain.R, plain.V, dR, dV, tol, E, edges)[3])
+            ms.append(OL.learned_apply(c, plain.R, plain.V, dR, dV, tol, E, edges, precision)[3])
     ms = np.array(ms)
     return np.all(ms < -amb, axis=0), np.all(ms > amb, axis=0)
 
@@ -354,6 +355,68 @@ def test_learned_step_network_matches_oracle_on_poisson(n):
     assert int(sure_fb.sum()) <= n_fb <= int(sure_fb.sum() + (~sure).sum())
     pic.pic_destroy(h)
     m.close()
+
+
+@pytest.mark.slow
+def test_full_size_learned_step_on_sampled_particles():
+    # The learned-stepper workload at full size in the launch configuration
+    # the bench times (10^7 particles, FP32 form, 512 cells, dt 0.4, sort
+    # every 4 steps) with a non-trivial network: a twin handle gives the
+    # plain step bit for bit, and on 20000 sampled particles the oracle
+    # decides the energy check from the interval of the network's output
+    # (oracle.mlp) and the frozen field of the deposit of y^n (oracle.learned)
+    n = 10_000_000
+    p = pic.pic_default_params(precision=1, dt=0.4, n_cells=512, sort_every=4)
+    c = cfg_of(p)
+    R0, V0 = inputs.gaussian_beam(n, seed=0, r_cut=4.0)
+    w = inputs.mlp_init(23)
+    rng = np.random.default_rng(24)
+    pp = omlp.unflatten(w.astype(np.float64))
+    for b in ("b1", "b2", "b3"):
+        pp[b] = rng.normal(0, 0.1, pp[b].shape)
+    w = omlp.flatten(pp).astype(np.float32)
+    scale, tol = (2.0 ** -8, 2.0 ** -8), 1e-3
+    m = pic.pic_mlp_create(16)
+    pic.pic_mlp_set_weights(m, w)
+    h = pic.pic_init(p, R0, V0)
+    twin = pic.pic_init(p, R0, V0)
+    n_fb = pic.pic_step_learned(h, m, 1, scale=scale, drift_tol=tol)
+    pic.pic_step(twin, 1)
+    R, V = pic.pic_get_particles(h)
+    Rp, Vp = pic.pic_get_particles(twin)
+    for x in (h, twin):
+        pic.pic_destroy(x)
+    m.close()
+    R0f = R0.astype(np.float32).astype(np.float64)
+    V0f = V0.astype(np.float32).astype(np.float64)
+    E, edges = OL.mesh_field(c, R0f, n, precision=1)
+    idx = np.sort(np.random.default_rng(25).choice(n, 20_000, replace=False))
+    X = OL.network_inputs(R0f[idx], V0f[idx], 0.0, c.eps, c.dt).astype(np.float64)
+    iv = omlp.forward_interval(w.astype(np.float64), X)["out"]
+    dR_lo, dR_hi = scale[0] * iv.lo[:, 0], scale[0] * iv.hi[:, 0]
+    dV_lo, dV_hi = scale[1] * iv.lo[:, 1], scale[1] * iv.hi[:, 1]
+
+    class Plain:
+        pass
+
+    plain = Plain()
+    plain.R, plain.V = Rp[idx], Vp[idx]
+    sure_keep, sure_fb = _oracle_certainty(c, plain, dR_lo, dR_hi, dV_lo, dV_hi, tol, E, edges, precision=1)
+    nonzero = ~((dR_lo <= 0) & (dR_hi >= 0) & (dV_lo <= 0) & (dV_hi >= 0))
+    sure_keep &= nonzero
+    sure_fb &= nonzero
+    assert (sure_keep | sure_fb).mean() > 0.95 and sure_keep.sum() > 1000 and sure_fb.sum() > 100, (
+        (sure_keep | sure_fb).mean(), sure_keep.sum(), sure_fb.sum())
+    Rs, Vs = R[idx], V[idx]
+    assert bit_equal(Rs[sure_fb], plain.R[sure_fb]) and bit_equal(Vs[sure_fb], plain.V[sure_fb])
+    f = np.float32
+    lo_R = (f(plain.R) + f(dR_lo)).astype(np.float64)
+    hi_R = (f(plain.R) + f(dR_hi)).astype(np.float64)
+    lo_V = (f(plain.V) + f(dV_lo)).astype(np.float64)
+    hi_V = (f(plain.V) + f(dV_hi)).astype(np.float64)
+    k = sure_keep
+    assert np.all((Rs[k] >= lo_R[k]) & (Rs[k] <= hi_R[k])) and np.all((Vs[k] >= lo_V[k]) & (Vs[k] <= hi_V[k]))
+    assert 0 < n_fb < n
 
 
 def _f32(x):
