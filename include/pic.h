@@ -275,11 +275,12 @@ int pic_poisson(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, 
    n_cells <= 16384) that every GPU which loads the library keeps until the
    process exits; larger meshes return PIC_ERR_TOO_LARGE and nothing runs.
    It calls no device allocation or free.  The first call on each device
-   looks up the array's device address (so make that first call before any
-   stream capture).  All calls share the one array: each call clears the
-   parts that must start at zero, and calls whose work overlaps on the GPU
-   (different streams, or different host threads, without ordering between
-   them) race on it.  The call synchronises `stream` to read the status. */
+   looks up the array's device address.  All calls share the one array:
+   each call clears the parts that must start at zero, and calls whose work
+   overlaps on the GPU (different streams, or different host threads,
+   without ordering between them) race on it.  Every call synchronises
+   `stream` to read the status, so it cannot be made while `stream` is
+   being captured into a graph. */
 int pic_poisson_noalloc(const pic_params* p, int64_t n_particles, const int64_t* Q_dev, double* E_dev,
                         double* rE_edges_dev, void* stream);
 
