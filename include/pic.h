@@ -399,19 +399,29 @@ int pic_batch_create(int32_t n_beams, const pic_params* params, const int64_t* n
 int pic_batch_step(pic_batch* b, int64_t n_steps);
 /* hist_copies: 1, 2 or 4 copies of each block's charge histogram (lane l
    of a warp deposits into copy l mod hist_copies); more copies take more
-   shared memory per block and may leave fewer blocks per SM. */
+   shared memory per block and may leave fewer blocks per SM.  The launch's
+   shared memory is sized for hist_copies copies of the largest mesh; a
+   Poisson beam with a smaller mesh uses up to 4 copies where they fit in
+   it, as long as each of its blocks deposits at least 2048 positions per
+   copy and cycle. */
 int pic_batch_set_config(pic_batch* b, int32_t block, int32_t blocks_per_sm, double alloc_power,
                          int32_t sort_every, int32_t hist_copies);
 int pic_batch_get_config(const pic_batch* b, pic_batch_config_t* out);
-/* Autotuner: times steps_per_trial macro steps (after one warm step) for
-   each launch shape (block size x blocks per SM x allocation power x
-   histogram copies) that fits, keeps the fastest, then times the sort
-   periods 1, 4, 16 and keeps the fastest.  Then it sets the block shares
-   from the beams' measured window times (each beam's time x blocks, as
-   its work) while that makes the step at least 0.5 % faster (at most 8
-   rounds).  The trial
-   steps are real steps of the batch (their results do not depend on the
-   shape or the shares).  *best receives the chosen configuration. */
+/* Autotuner.  For each launch shape (block size x blocks per SM x
+   allocation power x histogram copies) that fits, it runs one warm step and
+   steps_per_trial timed steps and keeps the shape with the shortest launch
+   span (first block start to last block end over all beams, device timer;
+   the sorts, which fall into some trials and not others, are not in it).
+   Then it times the sort periods 1, 4, 16 over whole periods (at least
+   steps_per_trial steps) and keeps the fastest step.  Then it sets block
+   shares from the beams' measured window times: a Poisson beam's window is
+   predicted to scale as 1/blocks, an analytic beam's with the particles
+   one thread advances in turn, and the shares that minimise the largest
+   prediction are timed; up to 8 rounds, each predicting from the last
+   trial, until two in a row do not shorten the best span by 0.5 %.  The
+   shares that timed best stay.  The trial steps are real steps of the
+   batch (their results do not depend on the shape or the shares).  *best
+   receives the chosen configuration. */
 int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* best);
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind);
 int pic_batch_set_particles(pic_batch* b, int32_t beam, const double* r, const double* v, int ptr_kind);

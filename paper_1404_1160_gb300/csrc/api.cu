@@ -1331,7 +1331,18 @@ cudaError_t batch_upload(pic_batch* b) {
         pic_handle* h = b->hs[i];
         pic::BeamDesc32& d = b->desc[i];
         d.P = h->dp;
-        d.P.hist_copies = b->copies;  // the batch's shared memory is sized for this many
+        // the batch's shared memory is sized for b->copies copies of the
+        // largest mesh; a beam with a smaller mesh takes up to four where
+        // they fit, while its blocks still deposit at least 2048 positions
+        // per copy and cycle (more copies spread same-cell atomics)
+        int cp = b->copies;
+        if (h->prm.field_model == PIC_FIELD_POISSON && d.n_blocks > 0) {
+            const long long per_block = (h->n + d.n_blocks - 1) / d.n_blocks;
+            while (cp < 4 && pic::window32_batch_smem(h->prm.n_cells, 2 * cp) <= b->smem &&
+                   per_block >= 2048ll * 2 * cp)
+                cp *= 2;
+        }
+        d.P.hist_copies = cp;
         d.B = h->B32;
         d.Tin = h->prm.periods_once ? h->Tin32 : nullptr;
         d.T_known = h->prm.periods_once ? 1 : 0;
@@ -1342,10 +1353,79 @@ cudaError_t batch_upload(pic_batch* b) {
     return cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(pic::BeamDesc32) * b->n, cudaMemcpyHostToDevice, b->st);
 }
 
+// Measured windows of the beams: beam i took ms[i] on blocks[i] blocks of
+// `block` threads.
+struct BeamTimes {
+    std::vector<double> ms;
+    std::vector<long long> blocks;
+    int block = 0;
+};
+
+// Blocks per beam that minimise the largest predicted window (min-max
+// greedy).  A Poisson beam's window is predicted as ms n_0 / n on n blocks
+// (its sweeps divide over the blocks); an analytic beam's as ms r(n) / r(n_0),
+// r(n) = ceil(particles / (n block)) being the particles one thread advances
+// one after the other.  Every beam starts at its least share lo[i]; then the
+// beam with the largest prediction that more blocks would shorten gets them
+// (one block, or for an analytic beam the blocks that take r one lower),
+// until the grid is used up or no beam can be shortened.
+static bool shares_minmax(const pic_batch* b, const BeamTimes& t, int block, long long G,
+                          const std::vector<long long>& lo, const std::vector<long long>& need,
+                          std::vector<long long>& nb) {
+    const int n = b->n;
+    std::vector<char> coop(n);
+    std::vector<long long> np(n);
+    for (int i = 0; i < n; ++i) {
+        coop[i] = b->hs[i]->prm.field_model == PIC_FIELD_POISSON;
+        np[i] = b->hs[i]->n > 0 ? b->hs[i]->n : 1;
+    }
+    auto rounds = [&](int i, long long m, int blk) { return (np[i] + m * blk - 1) / (m * blk); };
+    auto pred = [&](int i, long long m) -> double {
+        const double ms = std::max(t.ms[i], 1e-6);
+        if (coop[i]) return ms * (double)t.blocks[i] / (double)m;
+        return ms * (double)rounds(i, m, block) / (double)rounds(i, t.blocks[i], t.block);
+    };
+    long long used = 0;
+    for (int i = 0; i < n; ++i) {
+        nb[i] = lo[i];
+        used += nb[i];
+    }
+    if (used > G) return false;
+    for (;;) {
+        int best = -1;
+        long long best_to = 0;
+        double best_p = -1.0;
+        for (int i = 0; i < n; ++i) {
+            if (nb[i] >= need[i]) continue;
+            long long to = nb[i] + 1;
+            if (!coop[i]) {
+                // fewest blocks with one round less
+                const long long r = rounds(i, nb[i], block);
+                to = r > 1 ? (np[i] + (r - 1) * block - 1) / ((r - 1) * block) : need[i];
+                if (to > need[i]) to = need[i];
+                if (to <= nb[i]) to = nb[i] + 1;
+            }
+            if (used + (to - nb[i]) > G) continue;
+            const double p = pred(i, nb[i]);
+            if (p > best_p) {
+                best = i;
+                best_p = p;
+                best_to = to;
+            }
+        }
+        if (best < 0) break;
+        used += best_to - nb[best];
+        nb[best] = best_to;
+    }
+    return true;
+}
+
 // Blocks per beam in proportion to (its particles)^power, at least one and
 // at most what its particles fill; weight 1/4 for the analytic fields (no
-// field cycle).  wts (may be null): the beams' weights instead.
-int batch_configure(pic_batch* b, int block, int bps_want, double power, int copies, const double* wts = nullptr) {
+// field cycle).  meas (may be null): shares from the beams' measured
+// windows instead (shares_minmax).
+int batch_configure(pic_batch* b, int block, int bps_want, double power, int copies,
+                    const BeamTimes* meas = nullptr) {
     if (block < 128 || block > 1024 || (block & 31)) return PIC_ERR_INVALID_ARG;
     if (copies != 1 && copies != 2 && copies != 4) return PIC_ERR_INVALID_ARG;
     const size_t smem = pic::window32_batch_smem(b->max_cells, copies);
@@ -1364,7 +1444,7 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power, int cop
     const long long G = (long long)bps * b->sm_count;
     if (G < b->n) return PIC_ERR_UNSUPPORTED;
     std::vector<double> w(b->n);
-    std::vector<long long> need(b->n), nb(b->n);
+    std::vector<long long> need(b->n), lo(b->n), nb(b->n);
     double wsum = 0.0;
     for (int i = 0; i < b->n; ++i) {
         pic_handle* h = b->hs[i];
@@ -1372,30 +1452,38 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power, int cop
         const long long groups = (h->B32.ld + 127) / 128;
         need[i] = coop ? (groups + block / 32 - 1) / (block / 32) : (h->n + block - 1) / block;
         if (need[i] < 1) need[i] = 1;
-        w[i] = wts ? wts[i] : (coop ? 1.0 : 0.25) * std::pow((double)(h->n > 0 ? h->n : 1), power);
+        // a Poisson beam's blocks deposit at most 2^21 positions each per cycle
+        lo[i] = coop ? std::max(1ll, (groups * 128 + (1ll << 21) - 1) >> 21) : 1;
+        if (lo[i] > need[i]) need[i] = lo[i];
+        w[i] = (coop ? 1.0 : 0.25) * std::pow((double)(h->n > 0 ? h->n : 1), power);
         wsum += w[i];
     }
-    long long used = 0;
-    for (int i = 0; i < b->n; ++i) {
-        long long k = (long long)std::floor((double)(G - b->n) * w[i] / wsum) + 1;
-        nb[i] = k < need[i] ? k : need[i];
-        used += nb[i];
-    }
-    // hand out what is left, largest deficit first
-    while (used < G) {
-        int best = -1;
-        double bestd = 0.0;
+    if (meas && (int)meas->ms.size() == b->n && (int)meas->blocks.size() == b->n && meas->block > 0) {
+        if (!shares_minmax(b, *meas, block, G, lo, need, nb)) return PIC_ERR_UNSUPPORTED;
+    } else {
+        meas = nullptr;
+        long long used = 0;
         for (int i = 0; i < b->n; ++i) {
-            if (nb[i] >= need[i]) continue;
-            const double d = (double)G * w[i] / wsum - (double)nb[i];
-            if (best < 0 || d > bestd) {
-                best = i;
-                bestd = d;
-            }
+            long long k = (long long)std::floor((double)(G - b->n) * w[i] / wsum) + 1;
+            nb[i] = k < need[i] ? k : need[i];
+            used += nb[i];
         }
-        if (best < 0) break;
-        ++nb[best];
-        ++used;
+        // hand out what is left, largest deficit first
+        while (used < G) {
+            int best = -1;
+            double bestd = 0.0;
+            for (int i = 0; i < b->n; ++i) {
+                if (nb[i] >= need[i]) continue;
+                const double d = (double)G * w[i] / wsum - (double)nb[i];
+                if (best < 0 || d > bestd) {
+                    best = i;
+                    bestd = d;
+                }
+            }
+            if (best < 0) break;
+            ++nb[best];
+            ++used;
+        }
     }
     int first = 0;
     for (int i = 0; i < b->n; ++i) {
@@ -1412,7 +1500,7 @@ int batch_configure(pic_batch* b, int block, int bps_want, double power, int cop
     b->block = block;
     b->bps = bps;
     b->alloc_power = power;
-    b->shares_measured = wts != nullptr;
+    b->shares_measured = meas != nullptr;
     b->copies = copies;
     b->smem = smem;
     return map_cuda(batch_upload(b));
@@ -1605,20 +1693,36 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIC_ERR_CUDA;
     std::vector<double> beam_ms(b->n);  // each beam's mean window time over the last trial
-    auto trial = [&](double* ms) -> int {
+    // One trial: a step that captures and warms, then `steps` timed steps.
+    // *ms: the mean step (sorts, graph captures and host work included);
+    // *span: the mean launch span, first block start to last block end over
+    // all beams (device timer), which is what launch shapes and block shares
+    // change, without the sorts that fall into some trials and not others.
+    auto trial = [&](int steps, double* ms, double* span) -> int {
         int rc = batch_one_step(b);  // capture and warm
         if (rc) return rc;
         std::fill(beam_ms.begin(), beam_ms.end(), 0.0);
+        double sp = 0.0;
         cudaEventRecord(e0, b->st);
-        for (int s = 0; s < steps_per_trial && !rc; ++s) {
+        for (int s = 0; s < steps && !rc; ++s) {
             rc = batch_one_step(b);
-            for (int i = 0; i < b->n; ++i) beam_ms[i] += b->hs[i]->window_ms / steps_per_trial;
+            unsigned long long lo = ~0ull, hi = 0ull;
+            for (int i = 0; i < b->n; ++i) {
+                beam_ms[i] += b->hs[i]->window_ms / steps;
+                const unsigned long long t0 = b->h_times[2 * i], t1 = b->h_times[2 * i + 1];
+                if (t1 > t0) {
+                    lo = std::min(lo, t0);
+                    hi = std::max(hi, t1);
+                }
+            }
+            sp += hi > lo ? (double)(hi - lo) * 1e-6 / steps : 0.0;
         }
         cudaEventRecord(e1, b->st);
         cudaEventSynchronize(e1);
         float x = 0.f;
         cudaEventElapsedTime(&x, e0, e1);
-        *ms = (double)x / steps_per_trial;
+        *ms = (double)x / steps;
+        *span = sp > 0.0 ? sp : *ms;
         return rc;
     };
     double best_ms = 1e300;
@@ -1631,22 +1735,24 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
             rc = r;
             break;
         }
-        double ms = 0.0;
-        if ((rc = trial(&ms))) break;
-        if (ms < best_ms) {
-            best_ms = ms;
+        double ms = 0.0, span = 0.0;
+        if ((rc = trial(steps_per_trial, &ms, &span))) break;
+        if (span < best_ms) {
+            best_ms = span;
             bestc = c;
         }
     }
     if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies);
+    // sort periods: whole periods are timed (at least steps_per_trial steps),
+    // so that every trial holds one sort per period
     int best_sort = b->sort_every;
     if (!rc) {
         double best_sort_ms = 1e300;
         const int sorts[] = {1, 4, 16};
         for (int so : sorts) {
             b->sort_every = so;
-            double ms = 0.0;
-            if ((rc = trial(&ms))) break;
+            double ms = 0.0, span = 0.0;
+            if ((rc = trial((steps_per_trial + so - 1) / so * so, &ms, &span))) break;
             if (ms < best_sort_ms) {
                 best_sort_ms = ms;
                 best_sort = so;
@@ -1654,28 +1760,39 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
         }
         b->sort_every = best_sort;
     }
-    // Block shares from measured beam times: a beam whose window took t_i on
-    // n_i blocks did about t_i n_i block-time of work; shares in proportion
-    // to that, within the same limits, even the windows out.  Repeated while
-    // the step gets at least 0.5 % faster; the shares that timed best stay.
+    // Block shares from measured beam times (shares_minmax): the windows of
+    // the last trial predict each beam's window on other block counts, and
+    // the shares that minimise the largest prediction are tried next.  Up to
+    // eight rounds, ended by two in a row that do not beat the best launch
+    // span by 0.5 % (a slower trial still measures its own shares, so the
+    // next round predicts from it); the shares that timed best stay.
     if (!rc) {
-        double cur_ms = 0.0;
-        rc = trial(&cur_ms);
-        std::vector<double> cur_w;  // empty: the power-law shares
-        for (int it = 0; it < 8 && !rc; ++it) {
-            std::vector<double> w(b->n);
-            for (int i = 0; i < b->n; ++i) w[i] = std::max(beam_ms[i], 1e-6) * (double)b->desc[i].n_blocks;
-            const int r = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies, w.data());
+        double best_sh_ms = 0.0, ms0 = 0.0;
+        rc = trial(steps_per_trial, &ms0, &best_sh_ms);
+        BeamTimes best_t;  // empty: the power-law shares
+        int misses = 0;
+        for (int it = 0; it < 8 && !rc && misses < 2; ++it) {
+            BeamTimes t;
+            t.block = b->block;
+            t.ms = beam_ms;
+            t.blocks.resize(b->n);
+            for (int i = 0; i < b->n; ++i) t.blocks[i] = b->desc[i].n_blocks;
+            const int r = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies, &t);
             if (r == PIC_ERR_UNSUPPORTED) break;
             if ((rc = r)) break;
-            double ms = 0.0;
-            if ((rc = trial(&ms))) break;
-            if (!(ms < 0.995 * cur_ms)) break;
-            cur_ms = ms;
-            cur_w = w;
+            double ms = 0.0, span = 0.0;
+            if ((rc = trial(steps_per_trial, &ms, &span))) break;
+            if (span < 0.995 * best_sh_ms) {
+                best_sh_ms = span;
+                best_t = t;
+                misses = 0;
+            } else {
+                ++misses;
+            }
         }
-        if (!rc) rc = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies,
-                                      cur_w.empty() ? nullptr : cur_w.data());
+        if (!rc)
+            rc = batch_configure(b, bestc.block, bestc.bps, bestc.power, bestc.copies,
+                                 best_t.ms.empty() ? nullptr : &best_t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

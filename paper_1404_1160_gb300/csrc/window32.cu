@@ -528,12 +528,22 @@ __global__ void __launch_bounds__(kW32Threads, 1) k_window32_coop(DevParams P, W
 
 // ------------------------------------------- per-particle window (analytic E)
 
-// One fine step k -> k+1 of Lawson RK4 in the rotating frame, analytic field.
+// The per-particle loops below keep the table position of fine step k,
+// ia = 2k mod 2 spt, and advance it by one step with a compare instead of
+// a remainder by the run-time table length (which costs more than the
+// step's own arithmetic).  ia is even, so ia + 1 is always in the table.
+__device__ __forceinline__ int rot_next(const DevParams& P, int ia) {
+    const int t = ia + 2;
+    return t == 2 * P.spt ? 0 : t;
+}
+
+// One fine step k -> k+1 of Lawson RK4 in the rotating frame, analytic
+// field; ia = 2k mod 2 spt.
 template <int FIELD>
-__device__ __forceinline__ void step32_analytic(const DevParams& P, long long k, float& zR, float& zV) {
-    const float2 a = P.rot[rot_index(P, 2 * k)];
-    const float2 m = P.rot[rot_index(P, 2 * k + 1)];
-    const float2 b = P.rot[rot_index(P, 2 * k + 2)];
+__device__ __forceinline__ void step32_analytic(const DevParams& P, int ia, float& zR, float& zV) {
+    const float2 a = P.rot[ia];
+    const float2 m = P.rot[ia + 1];
+    const float2 b = P.rot[rot_next(P, ia)];
     const float R3 = rot_R(m, zR, zV);
     const float e1 = field_analytic32(FIELD, rot_R(a, zR, zV));
     const float e3 = field_analytic32(FIELD, R3);
@@ -542,9 +552,13 @@ __device__ __forceinline__ void step32_analytic(const DevParams& P, long long k,
     lawson32_update(P, a, m, b, e1, e2, e3, e4, zR, zV);
 }
 
-__device__ __forceinline__ float2 y_of(const DevParams& P, long long k, float zR, float zV) {
-    const float2 cs = P.rot[rot_index(P, 2 * k)];
+// y = Phi(t_k) z with ia = 2k mod 2 spt (y_at) or any k (y_of).
+__device__ __forceinline__ float2 y_at(const DevParams& P, int ia, float zR, float zV) {
+    const float2 cs = P.rot[ia];
     return make_float2(rot_R(cs, zR, zV), rot_V(cs, zR, zV));
+}
+__device__ __forceinline__ float2 y_of(const DevParams& P, long long k, float zR, float zV) {
+    return y_at(P, rot_index(P, 2 * k), zR, zV);
 }
 
 template <int FIELD>
@@ -557,8 +571,12 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
         const float2 y0 = B.y[i];
         float zR = y0.x, zV = y0.y;
         if (mode == MODE_FINE) {
-            for (long long k = 0; k < n_iter; ++k) step32_analytic<FIELD>(P, k, zR, zV);
-            B.y[i] = y_of(P, n_iter, zR, zV);
+            int ia = 0;
+            for (long long k = 0; k < n_iter; ++k) {
+                step32_analytic<FIELD>(P, ia, zR, zV);
+                ia = rot_next(P, ia);
+            }
+            B.y[i] = y_at(P, ia, zR, zV);
             continue;
         }
         if (mode == MODE_PERIODS) {
@@ -568,7 +586,7 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
             t1.f = 0.0f;
             T = t1;
             float vkm2 = 0.0f, vkm1 = zV;
-            int K = 0;
+            int K = 0, ia = 0;
             for (;;) {
                 if (flags & F_RES) break;
                 if (K == P.Kmax) {
@@ -577,9 +595,10 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
                     T.f = 0.0f;
                     break;
                 }
-                step32_analytic<FIELD>(P, K, zR, zV);
+                step32_analytic<FIELD>(P, ia, zR, zV);
+                ia = rot_next(P, ia);
                 ++K;
-                const float v = y_of(P, K, zR, zV).y;
+                const float v = y_at(P, ia, zR, zV).y;
                 if (K >= 2 && positive32(vkm2) != positive32(vkm1)) {
                     const float s = quad_root01f(vkm2, vkm1, v);
                     const int ne = (flags & F_NEXT) + 1;
@@ -617,20 +636,22 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
                 const int k2 = d.N > 0 ? u2.i : -10;
                 float a[3], b[3], c[3], e[3];
                 K = 0;
+                int ia = 0;
                 for (;;) {
                     const int r1 = K - k1, r2 = K - k2;
                     if (r1 >= 0 && r1 < 3) {
-                        const float2 y = y_of(P, K, zR, zV);
+                        const float2 y = y_at(P, ia, zR, zV);
                         a[r1] = y.x;
                         b[r1] = y.y;
                     }
                     if (r2 >= 0 && r2 < 3) {
-                        const float2 y = y_of(P, K, zR, zV);
+                        const float2 y = y_at(P, ia, zR, zV);
                         c[r2] = y.x;
                         e[r2] = y.y;
                     }
                     if (K >= d.need) break;
-                    step32_analytic<FIELD>(P, K, zR, zV);
+                    step32_analytic<FIELD>(P, ia, zR, zV);
+                    ia = rot_next(P, ia);
                     ++K;
                 }
                 ya[0] = interp3f(a[0], a[1], a[2], d.o.f);
@@ -650,6 +671,7 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
                 t1.f = 0.0f;
                 float vkm2 = 0.0f, vkm1 = zV;
                 K = 0;
+                int ia = 0;
                 B.y[i] = make_float2(zR, zV);
                 for (;;) {
                     if ((fl & F_RES) && K >= d.need) break;
@@ -663,10 +685,11 @@ __device__ __forceinline__ void window32_local_body(const DevParams& P, const Wi
                         }
                         break;
                     }
-                    step32_analytic<FIELD>(P, K, zR, zV);
+                    step32_analytic<FIELD>(P, ia, zR, zV);
+                    ia = rot_next(P, ia);
                     ++K;
                     B.traj[(size_t)(K - 1) * ld + i] = make_float2(zR, zV);
-                    const float v = y_of(P, K, zR, zV).y;
+                    const float v = y_at(P, ia, zR, zV).y;
                     if (!(fl & F_RES) && K >= 2 && positive32(vkm2) != positive32(vkm1)) {
                         const float s = quad_root01f(vkm2, vkm1, v);
                         const int ne = (fl & F_NEXT) + 1;

@@ -93,7 +93,7 @@ def test_batch_equals_single_beams_and_ignores_the_launch_shape():
 
 def test_autotuner_steps_are_real_steps():
     beams = make_beams()
-    ref = single_runs(beams, 1 + 15 * 3 + 3 * 3 + 9 * 3 + 2)
+    ref = single_runs(beams, TUNE_STEPS_MAX)
     b = pic.pic_batch_create([make_params(sp) for sp in SPECS], beams)
     pic.pic_batch_step(b, 1)
     best = pic.pic_batch_tune(b, steps_per_trial=2)
@@ -107,10 +107,15 @@ def test_autotuner_steps_are_real_steps():
     b.close()
 
 
+# steps_per_trial = 2: a trial is a warm step plus the timed steps.  One
+# step, up to 15 launch shapes (3 steps each), the sort periods 1, 4, 16
+# timed over whole periods (3, 5 and 17 steps), up to 9 trials of measured
+# block shares (3 steps each) and 2 more steps bound what the tuner runs.
+TUNE_STEPS_MAX = 1 + 15 * 3 + (3 + 5 + 17) + 9 * 3 + 2
+
+
 def ref_steps(done):
-    # the reference above ran 1 + (up to 15 shapes + 3 sort periods + up to 9
-    # trials of measured block shares) x 3 + 2 steps
-    return 1 + 15 * 3 + 3 * 3 + 9 * 3 + 2 - done
+    return TUNE_STEPS_MAX - done
 
 
 def test_batch_rejects_the_fp64_path():
