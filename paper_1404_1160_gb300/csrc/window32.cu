@@ -54,6 +54,80 @@ __device__ __forceinline__ void deposit32(unsigned int* h, int Np1, int j, unsig
     if (ok && c) atomicAdd(hj + 3 * Np1, c);
 }
 
+// deposit32 of a cell known to be on the mesh (j >= 0)
+__device__ __forceinline__ void deposit32_on(unsigned int* h, int Np1, int j, unsigned int qR) {
+    unsigned int* hj = h + j;
+    const unsigned int a = qR & 0x7ffu, b = (qR >> 11) & 0x7ffu, c = qR >> 22;
+    atomicAdd(hj, 1u);
+    if (a) atomicAdd(hj + Np1, a);
+    if (b) atomicAdd(hj + 2 * Np1, b);
+    if (c) atomicAdd(hj + 3 * Np1, c);
+}
+
+// ------------------------------------------ located pairs, warp-uniform path
+//
+// Nearly every warp has all its positions on the mesh.  The pair helpers
+// below test that once per pair of positions (one warp vote) and then run
+// the cell arithmetic without the off-mesh selects, the gather without the
+// edge division and the deposit without the on-mesh test; a warp with a lane
+// off the mesh (or at a NaN) runs the general locate32t / gather32 /
+// deposit32.  Both give the same cells, weights, fields and words.  Every
+// lane of the warp must make the call.
+
+// Cell of an on-mesh x = (R - r_min)/h_r, 0 <= x < n_cells: the general
+// locate32t with its test known true.
+template <bool NEED_Q>
+__device__ __forceinline__ Cell32 cell_on_mesh(const DevParams& P, float x) {
+    const float fl = floorf(x);
+    const float f = x - fl;
+    Cell32 c;
+    c.j = (int)fl;
+    c.a = f;
+    c.qR = NEED_Q ? __float2uint_rz(f * P.Wf) : 0u;
+    return c;
+}
+
+// true when every lane of the warp has both positions on the mesh
+__device__ __forceinline__ bool warp_on_mesh(const DevParams& P, float xa, float xb) {
+    const bool in = xa >= 0.0f && xa < P.ncells_f && xb >= 0.0f && xb < P.ncells_f;
+    return __all_sync(0xffffffffu, in);
+}
+
+// Fields at Ra (table ta, edges ed[0..1]) and Rb (table tb, edges ed[2..3]).
+__device__ __forceinline__ void locate_gather2(const DevParams& P, float Ra, float Rb, const float2* ta,
+                                               const float2* tb, const float* ed, float& ea, float& eb) {
+    const float xa = (Ra - P.r_min_f) * P.inv_hr_f, xb = (Rb - P.r_min_f) * P.inv_hr_f;
+    if (warp_on_mesh(P, xa, xb)) {
+        const Cell32 ca = cell_on_mesh<false>(P, xa), cb = cell_on_mesh<false>(P, xb);
+        const float2 va = ta[ca.j], vb = tb[cb.j];
+        ea = fmaf(ca.a, va.y, va.x);
+        eb = fmaf(cb.a, vb.y, vb.x);
+    } else {
+        const Cell32 ca = locate32t<false>(P, Ra), cb = locate32t<false>(P, Rb);
+        ea = gather32(ta, ed[0], ed[1], ca);
+        eb = gather32(tb, ed[2], ed[3], cb);
+    }
+}
+
+// Deposits Ra into ha and Rb into hb when `valid`.
+__device__ __forceinline__ void locate_deposit2(const DevParams& P, float Ra, float Rb, unsigned int* ha,
+                                                unsigned int* hb, int Np1, bool valid) {
+    const float xa = (Ra - P.r_min_f) * P.inv_hr_f, xb = (Rb - P.r_min_f) * P.inv_hr_f;
+    if (warp_on_mesh(P, xa, xb)) {
+        const Cell32 ca = cell_on_mesh<true>(P, xa), cb = cell_on_mesh<true>(P, xb);
+        if (valid) {
+            deposit32_on(ha, Np1, ca.j, ca.qR);
+            deposit32_on(hb, Np1, cb.j, cb.qR);
+        }
+    } else {
+        const Cell32 ca = locate32(P, Ra), cb = locate32(P, Rb);
+        if (valid) {
+            deposit32(ha, Np1, ca.j, ca.qR);
+            deposit32(hb, Np1, cb.j, cb.qR);
+        }
+    }
+}
+
 __device__ __forceinline__ unsigned long long hist32_S(const unsigned int* h, int Np1, int j) {
     return (unsigned long long)h[Np1 + j] + ((unsigned long long)h[2 * Np1 + j] << 11) +
            ((unsigned long long)h[3 * Np1 + j] << 22);
@@ -390,10 +464,9 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
                 if (k > 0) {
                     const float R3 = rot_R(rm, zR, zV);
                     const float e1 = grp_e(cur, 2 * q), e3 = grp_e(cur, 2 * q + 1);
-                    const Cell32 c2 = locate32t<false>(P, lawson32_R2(P, R3, e1));
-                    const Cell32 c4 = locate32t<false>(P, lawson32_R4(P, rb, zR, zV, e3));
-                    const float e2 = gather32(tabB, s_edB[0], s_edB[1], c2);
-                    const float e4 = gather32(tabB + Np1, s_edB[2], s_edB[3], c4);
+                    float e2, e4;
+                    locate_gather2(P, lawson32_R2(P, R3, e1), lawson32_R4(P, rb, zR, zV, e3), tabB, tabB + Np1,
+                                   s_edB, e2, e4);
                     const float Vold = rot_V(ra, zR, zV);
                     lawson32_update(P, ra, rm, rb, e1, e2, e3, e4, zR, zV);
                     if (track && valid) {
@@ -414,12 +487,7 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
                 zo[2 * q] = zR;
                 zo[2 * q + 1] = zV;
                 // stage pair 1 of step k: R1 = (Phi(t_k) z)_R, R3 = (Phi(t_k + h/2) z)_R
-                const Cell32 d1 = locate32(P, rot_R(rb, zR, zV));
-                const Cell32 d3 = locate32(P, rot_R(rp, zR, zV));
-                if (valid) {
-                    deposit32(histA, Np1, d1.j, d1.qR);
-                    deposit32(histB, Np1, d3.j, d3.qR);
-                }
+                locate_deposit2(P, rot_R(rb, zR, zV), rot_R(rp, zR, zV), histA, histB, Np1, valid);
             }
             if (k > 0) {
                 float4* o = (float4*)(dst + base);
@@ -460,19 +528,12 @@ __device__ __forceinline__ void window32_coop_body(const DevParams& P, const Win
             for (int q = 0; q < kG; ++q) {
                 const bool valid = base + q < n;
                 const float zR = grp_get(cur, 2 * q), zV = grp_get(cur, 2 * q + 1);
-                const Cell32 c1 = locate32t<false>(P, rot_R(rb, zR, zV));
                 const float R3 = rot_R(rp, zR, zV);
-                const Cell32 c3 = locate32t<false>(P, R3);
-                const float e1 = gather32(tabA, s_edA[0], s_edA[1], c1);
-                const float e3 = gather32(tabA + Np1, s_edA[2], s_edA[3], c3);
+                float e1, e3;
+                locate_gather2(P, rot_R(rb, zR, zV), R3, tabA, tabA + Np1, s_edA, e1, e3);
                 eo[2 * q] = e1;
                 eo[2 * q + 1] = e3;
-                const Cell32 c2 = locate32(P, lawson32_R2(P, R3, e1));
-                const Cell32 c4 = locate32(P, lawson32_R4(P, rq, zR, zV, e3));
-                if (valid) {
-                    deposit32(histA, Np1, c2.j, c2.qR);
-                    deposit32(histB, Np1, c4.j, c4.qR);
-                }
+                locate_deposit2(P, lawson32_R2(P, R3, e1), lawson32_R4(P, rq, zR, zV, e3), histA, histB, Np1, valid);
             }
             float4* o = (float4*)(B.ce + base);
             o[0] = make_float4(eo[0], eo[1], eo[2], eo[3]);
