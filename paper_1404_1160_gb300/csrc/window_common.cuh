@@ -98,9 +98,15 @@ static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, co
     const long long incl = warp_incl_scan64(L);
     if (lane == 31) s_tot[f * 32 + w] = incl;
     __syncthreads();
+    // warps whose first node lies beyond the mesh own no node (warp-uniform)
+    const bool owns = w * 31 * R <= Nc;
     long long g0 = incl - L;
-    for (int v = 0; v < w; ++v) g0 += s_tot[f * 32 + v];
-    {
+    if (owns) {
+        // totals of the preceding warps of the half (w <= 15), summed by a butterfly
+        long long t = lane < w ? s_tot[f * 32 + lane] : 0ll;
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        g0 += t;
         long long g = g0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -109,6 +115,7 @@ static __device__ __forceinline__ void field_build_regs_r(const DevParams& P, co
         }
     }
     __syncthreads();
+    if (!owns) return;
     const long long gc = s_tot[f * 32 + 16];
     auto value = [&](int j, long long S, long long qj) -> Val { return j > Nc ? Val(0) : field_at(j, S, qj); };
     long long S = g0 - gc;
