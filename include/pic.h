@@ -441,6 +441,23 @@ void pic_batch_destroy(pic_batch* b);
    works; the device stays usable.  Exercises the failure path of every
    device-side wait without faulting the GPU. */
 int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* stream);
+/* The block shares pic_batch_tune gives from measured windows, on plain
+   arrays (host arithmetic only: no device call, no GPU needed).  Beam i
+   (poisson[i] != 0: Poisson field, else analytic; n_particles[i] >= 1)
+   took window_ms[i] on blocks_measured[i] blocks of block_measured
+   threads.  Its window on b blocks of `block` threads is predicted as
+   window_ms * blocks_measured / b (Poisson) or window_ms * r(b) / r_measured
+   with r = ceil(n_particles / (blocks x threads)), the particles one thread
+   advances in turn (analytic).  blocks_out[i] lies in [least[i], most[i]],
+   their sum is at most `grid`, and the largest predicted window is the
+   least any such shares reach (min-max greedy: the beam with the largest
+   prediction that more blocks shorten takes them, one block or, for an
+   analytic beam, the blocks that remove one particle per thread).  Returns
+   PIC_ERR_INVALID_ARG for bad arguments, PIC_ERR_UNSUPPORTED when the
+   least shares exceed `grid`. */
+int pic_test_batch_shares(int32_t n_beams, const int32_t* poisson, const int64_t* n_particles, const double* window_ms,
+                          const int64_t* blocks_measured, int32_t block_measured, int32_t block, int64_t grid,
+                          const int64_t* least, const int64_t* most, int64_t* blocks_out);
 
 #ifdef __cplusplus
 }

@@ -1353,37 +1353,26 @@ cudaError_t batch_upload(pic_batch* b) {
     return cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(pic::BeamDesc32) * b->n, cudaMemcpyHostToDevice, b->st);
 }
 
-// Measured windows of the beams: beam i took ms[i] on blocks[i] blocks of
-// `block` threads.
-struct BeamTimes {
-    std::vector<double> ms;
-    std::vector<long long> blocks;
-    int block = 0;
-};
-
 // Blocks per beam that minimise the largest predicted window (min-max
-// greedy).  A Poisson beam's window is predicted as ms n_0 / n on n blocks
-// (its sweeps divide over the blocks); an analytic beam's as ms r(n) / r(n_0),
-// r(n) = ceil(particles / (n block)) being the particles one thread advances
-// one after the other.  Every beam starts at its least share lo[i]; then the
-// beam with the largest prediction that more blocks would shorten gets them
-// (one block, or for an analytic beam the blocks that take r one lower),
-// until the grid is used up or no beam can be shortened.
-static bool shares_minmax(const pic_batch* b, const BeamTimes& t, int block, long long G,
-                          const std::vector<long long>& lo, const std::vector<long long>& need,
-                          std::vector<long long>& nb) {
-    const int n = b->n;
-    std::vector<char> coop(n);
-    std::vector<long long> np(n);
-    for (int i = 0; i < n; ++i) {
-        coop[i] = b->hs[i]->prm.field_model == PIC_FIELD_POISSON;
-        np[i] = b->hs[i]->n > 0 ? b->hs[i]->n : 1;
-    }
+// greedy), on plain arrays.  Beam i (coop[i]: Poisson, else an analytic
+// field; np[i] particles) took ms[i] on blocks_meas[i] blocks of
+// block_meas threads.  A Poisson beam's window is predicted as
+// ms n_0 / n on n blocks (its sweeps divide over the blocks); an analytic
+// beam's as ms r(n) / r(n_0), r(n) = ceil(np / (n block)) being the
+// particles one thread advances one after the other.  Every beam starts at
+// its least share lo[i]; then the beam with the largest prediction that
+// more blocks would shorten gets them (one block, or for an analytic beam
+// the blocks that take r one lower), within need[i] and the grid G, until
+// the grid is used up or no beam can be shortened.  false: the least
+// shares exceed G.
+static bool shares_minmax_core(int n, const char* coop, const long long* np, const double* ms,
+                               const long long* blocks_meas, int block_meas, int block, long long G,
+                               const long long* lo, const long long* need, long long* nb) {
     auto rounds = [&](int i, long long m, int blk) { return (np[i] + m * blk - 1) / (m * blk); };
     auto pred = [&](int i, long long m) -> double {
-        const double ms = std::max(t.ms[i], 1e-6);
-        if (coop[i]) return ms * (double)t.blocks[i] / (double)m;
-        return ms * (double)rounds(i, m, block) / (double)rounds(i, t.blocks[i], t.block);
+        const double t = std::max(ms[i], 1e-6);
+        if (coop[i]) return t * (double)blocks_meas[i] / (double)m;
+        return t * (double)rounds(i, m, block) / (double)rounds(i, blocks_meas[i], block_meas);
     };
     long long used = 0;
     for (int i = 0; i < n; ++i) {
@@ -1418,6 +1407,29 @@ static bool shares_minmax(const pic_batch* b, const BeamTimes& t, int block, lon
         nb[best] = best_to;
     }
     return true;
+}
+
+// Measured windows of the beams: beam i took ms[i] on blocks[i] blocks of
+// `block` threads.
+struct BeamTimes {
+    std::vector<double> ms;
+    std::vector<long long> blocks;
+    int block = 0;
+};
+
+// shares_minmax_core for the beams of a batch.
+static bool shares_minmax(const pic_batch* b, const BeamTimes& t, int block, long long G,
+                          const std::vector<long long>& lo, const std::vector<long long>& need,
+                          std::vector<long long>& nb) {
+    const int n = b->n;
+    std::vector<char> coop(n);
+    std::vector<long long> np(n);
+    for (int i = 0; i < n; ++i) {
+        coop[i] = b->hs[i]->prm.field_model == PIC_FIELD_POISSON;
+        np[i] = b->hs[i]->n > 0 ? b->hs[i]->n : 1;
+    }
+    return shares_minmax_core(n, coop.data(), np.data(), t.ms.data(), t.blocks.data(), t.block, block, G, lo.data(),
+                              need.data(), nb.data());
 }
 
 // Blocks per beam in proportion to (its particles)^power, at least one and
@@ -1798,6 +1810,34 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
     cudaEventDestroy(e1);
     if (rc) return rc;
     return pic_batch_get_config(b, best);
+}
+
+int pic_test_batch_shares(int32_t n_beams, const int32_t* poisson, const int64_t* n_particles, const double* window_ms,
+                          const int64_t* blocks_measured, int32_t block_measured, int32_t block, int64_t grid,
+                          const int64_t* least, const int64_t* most, int64_t* blocks_out) {
+    if (n_beams < 1 || !poisson || !n_particles || !window_ms || !blocks_measured || !least || !most || !blocks_out ||
+        block_measured < 1 || block < 1 || grid < 1)
+        return PIC_ERR_INVALID_ARG;
+    const int n = n_beams;
+    std::vector<char> coop(n);
+    std::vector<long long> np(n), bm(n), lo(n), need(n), nb(n);
+    std::vector<double> ms(n);
+    for (int i = 0; i < n; ++i) {
+        if (n_particles[i] < 1 || blocks_measured[i] < 1 || least[i] < 1 || most[i] < least[i] ||
+            !(window_ms[i] >= 0.0))
+            return PIC_ERR_INVALID_ARG;
+        coop[i] = poisson[i] != 0;
+        np[i] = n_particles[i];
+        bm[i] = blocks_measured[i];
+        lo[i] = least[i];
+        need[i] = most[i];
+        ms[i] = window_ms[i];
+    }
+    if (!shares_minmax_core(n, coop.data(), np.data(), ms.data(), bm.data(), block_measured, block, grid, lo.data(),
+                            need.data(), nb.data()))
+        return PIC_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; ++i) blocks_out[i] = nb[i];
+    return PIC_OK;
 }
 
 int pic_batch_get_particles(pic_batch* b, int32_t beam, double* r, double* v, int ptr_kind) {

@@ -152,6 +152,7 @@ def load() -> C.CDLL:
             "pic_gather": (i32, [P(pic_params), i64, vp, vp, vp, vp, vp]),
             "pic_frozen_potential": (i32, [P(pic_params), vp, vp, vp, i64, vp, vp, vp]),
             "pic_test_barrier_timeout": (i32, [i64, i32, vp]),
+            "pic_test_batch_shares": (i32, [i32, vp, vp, vp, vp, i32, i32, i64, vp, vp, vp]),
             "pic_mlp_num_params": (i32, []),
             "pic_mlp_create": (i32, [i64, vp, P(vp)]),
             "pic_mlp_set_weights": (i32, [vp, vp, i32]),
@@ -384,6 +385,26 @@ def pic_frozen_potential(params: pic_params, E_dev, edges_dev, psi_nodes_dev, R_
 def pic_test_barrier_timeout(wait_limit_ns: int, stream=None, precision: int = 0) -> int:
     """Returns the raw status (PIC_ERR_TIMEOUT expected)."""
     return int(load().pic_test_barrier_timeout(wait_limit_ns, precision, _stream(stream)))
+
+
+def pic_test_batch_shares(poisson, n_particles, window_ms, blocks_measured, block_measured: int, block: int,
+                          grid: int, least, most):
+    """Block shares the batch tuner gives from measured windows (host only).
+    Returns (status, blocks) with blocks an int64 array, one entry per beam."""
+    n = len(n_particles)
+    pz = np.ascontiguousarray(poisson, dtype=np.int32)
+    npart = np.ascontiguousarray(n_particles, dtype=np.int64)
+    ms = np.ascontiguousarray(window_ms, dtype=np.float64)
+    bm = np.ascontiguousarray(blocks_measured, dtype=np.int64)
+    lo = np.ascontiguousarray(least, dtype=np.int64)
+    hi = np.ascontiguousarray(most, dtype=np.int64)
+    if not (pz.size == ms.size == bm.size == lo.size == hi.size == n):
+        raise ValueError("pic_test_batch_shares: every array needs one entry per beam")
+    out = np.zeros(n, dtype=np.int64)
+    rc = load().pic_test_batch_shares(n, pz.ctypes.data, npart.ctypes.data, ms.ctypes.data, bm.ctypes.data,
+                                      int(block_measured), int(block), int(grid), lo.ctypes.data, hi.ctypes.data,
+                                      out.ctypes.data)
+    return int(rc), out
 
 
 # ------------------------------------------------------------ learned stepper
