@@ -453,8 +453,10 @@ int pic_test_barrier_timeout(int64_t wait_limit_ns, int32_t precision, void* str
    least any such shares reach (min-max greedy: the beam with the largest
    prediction that more blocks shorten takes them, one block or, for an
    analytic beam, the blocks that remove one particle per thread).  Returns
-   PIC_ERR_INVALID_ARG for bad arguments, PIC_ERR_UNSUPPORTED when the
-   least shares exceed `grid`. */
+   PIC_ERR_INVALID_ARG for bad arguments (a count or block size below 1,
+   most < least, a negative or non-finite time, block sizes above 2^20,
+   block counts or grid above 2^31, particle counts above 2^62),
+   PIC_ERR_UNSUPPORTED when the least shares exceed `grid`. */
 int pic_test_batch_shares(int32_t n_beams, const int32_t* poisson, const int64_t* n_particles, const double* window_ms,
                           const int64_t* blocks_measured, int32_t block_measured, int32_t block, int64_t grid,
                           const int64_t* least, const int64_t* most, int64_t* blocks_out);

@@ -1815,16 +1815,19 @@ int pic_batch_tune(pic_batch* b, int32_t steps_per_trial, pic_batch_config_t* be
 int pic_test_batch_shares(int32_t n_beams, const int32_t* poisson, const int64_t* n_particles, const double* window_ms,
                           const int64_t* blocks_measured, int32_t block_measured, int32_t block, int64_t grid,
                           const int64_t* least, const int64_t* most, int64_t* blocks_out) {
+    // bounds that keep blocks x threads + particles inside int64
     if (n_beams < 1 || !poisson || !n_particles || !window_ms || !blocks_measured || !least || !most || !blocks_out ||
-        block_measured < 1 || block < 1 || grid < 1)
+        block_measured < 1 || block < 1 || block_measured > (1 << 20) || block > (1 << 20) || grid < 1 ||
+        grid > (1ll << 31))
         return PIC_ERR_INVALID_ARG;
     const int n = n_beams;
     std::vector<char> coop(n);
     std::vector<long long> np(n), bm(n), lo(n), need(n), nb(n);
     std::vector<double> ms(n);
     for (int i = 0; i < n; ++i) {
-        if (n_particles[i] < 1 || blocks_measured[i] < 1 || least[i] < 1 || most[i] < least[i] ||
-            !(window_ms[i] >= 0.0))
+        if (n_particles[i] < 1 || n_particles[i] > (1ll << 62) || blocks_measured[i] < 1 ||
+            blocks_measured[i] > (1ll << 31) || least[i] < 1 || most[i] < least[i] || most[i] > (1ll << 31) ||
+            !(window_ms[i] >= 0.0) || !std::isfinite(window_ms[i]))
             return PIC_ERR_INVALID_ARG;
         coop[i] = poisson[i] != 0;
         np[i] = n_particles[i];

@@ -119,3 +119,7 @@ def test_errors(pic):
     assert call(pic, bad)[0] == pic.PIC_ERR_INVALID_ARG
     bad = dict(case, lo=[1, 1], block=0)
     assert call(pic, bad)[0] == pic.PIC_ERR_INVALID_ARG
+    bad = dict(case, lo=[1, 1], ms=[float("nan"), 1.0])
+    assert call(pic, bad)[0] == pic.PIC_ERR_INVALID_ARG
+    bad = dict(case, lo=[1, 1], hi=[4, 1 << 40])  # block counts beyond 2^31
+    assert call(pic, bad)[0] == pic.PIC_ERR_INVALID_ARG
